@@ -1,0 +1,289 @@
+"""Python access to the plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+The oracle is the slow, literal C implementation in ``maxent_oracle.c`` of the
+maximum-entropy 5- and 14-moment method (Boccelli et al., JCP 2024).  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "maxent_oracle.c")
+_LIB = os.path.join(_HERE, "libmaxent_oracle.so")
+
+BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
+FLUX_HLL, FLUX_RUSANOV = 0, 1
+LIM_MINMOD, LIM_VANALBADA = 0, 1
+TAU_NONE, TAU_CONST, TAU_HARDSPHERE = 0, 1, 2
+FE, RK2 = 0, 1
+MAX_SPANS = 4
+MARGIN = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "maxent_oracle.h"))
+    ):
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class Side(C.Structure):
+    _fields_ = [
+        ("base_type", C.c_int),
+        ("base_state", C.c_double * 14),
+        ("nspans", C.c_int),
+        ("span_lo", C.c_double * MAX_SPANS),
+        ("span_hi", C.c_double * MAX_SPANS),
+        ("span_state", (C.c_double * 14) * MAX_SPANS),
+    ]
+
+
+class Cfg(C.Structure):
+    _fields_ = [
+        ("system", C.c_int),
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+        ("order", C.c_int), ("integrator", C.c_int), ("flux", C.c_int), ("limiter", C.c_int),
+        ("cfl", C.c_double), ("sigma_lim", C.c_double), ("k_ws", C.c_double),
+        ("tau_model", C.c_int),
+        ("tau_ref", C.c_double), ("rho_ref", C.c_double), ("T_ref", C.c_double),
+        ("side", Side * 4),
+    ]
+
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        for name in ("or5_prim2cons", "or5_cons2prim", "or14_prim2cons", "or14_cons2prim"):
+            getattr(L, name).argtypes = [_dp, _dp]
+            getattr(L, name).restype = None
+        L.or5_sigma.argtypes = [_dp]; L.or5_sigma.restype = C.c_double
+        L.or14_sigma.argtypes = [_dp]; L.or14_sigma.restype = C.c_double
+        L.or5_closure.argtypes = [_dp, C.c_double]; L.or5_closure.restype = C.c_double
+        L.or5_flux_given_s.argtypes = [_dp, C.c_double, _dp]; L.or5_flux_given_s.restype = None
+        L.or5_flux.argtypes = [_dp, C.c_double, _dp]; L.or5_flux.restype = None
+        L.or5_lambda_star_max.argtypes = [C.c_double, C.c_double]
+        L.or5_lambda_star_max.restype = C.c_double
+        L.or5_wavespeeds.argtypes = [_dp, C.c_double, C.c_double,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.or5_wavespeeds.restype = None
+        L.or5_source.argtypes = [_dp, C.c_double, _dp]; L.or5_source.restype = None
+        L.or14_closure.argtypes = [_dp, C.c_double, _dp, _dp, _dp]
+        L.or14_closure.restype = None
+        L.or14_flux_given_closure.argtypes = [_dp, _dp, _dp, _dp, C.c_int, _dp]
+        L.or14_flux_given_closure.restype = None
+        L.or14_flux.argtypes = [_dp, C.c_double, C.c_int, _dp]; L.or14_flux.restype = None
+        L.or14_lambda_star_max.argtypes = [C.c_double] * 4
+        L.or14_lambda_star_max.restype = C.c_double
+        L.or14_wavespeeds.argtypes = [_dp, C.c_int, C.c_double, C.c_double,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.or14_wavespeeds.restype = None
+        L.or14_source.argtypes = [_dp, C.c_double, _dp]; L.or14_source.restype = None
+        L.or_block_step.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
+                                    _dp, C.c_double, _dp]
+        L.or_block_step.restype = C.c_int
+        L.or_block_residual.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
+                                        _dp, _dp]
+        L.or_block_residual.restype = C.c_int
+        L.or_max_rate.argtypes = [C.POINTER(Cfg), _dp]; L.or_max_rate.restype = C.c_double
+        L.or_dt.argtypes = [C.POINTER(Cfg), _dp, C.c_double, C.c_double]
+        L.or_dt.restype = C.c_double
+        L.or_step.argtypes = [C.POINTER(Cfg), _dp, C.c_double]; L.or_step.restype = C.c_int
+        L.or_run.argtypes = [C.POINTER(Cfg), _dp, C.POINTER(C.c_double), C.c_double,
+                             C.c_int, C.c_void_p]
+        L.or_run.restype = C.c_int
+        L.or_tau.argtypes = [C.POINTER(Cfg), _dp]; L.or_tau.restype = C.c_double
+    return _lib
+
+
+def _a(x, n=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if n is not None:
+        assert a.shape == (n,), a.shape
+    return a
+
+
+# ---------------------------------------------------------------- point API
+def prim2cons(Q):
+    Q = _a(Q); U = np.empty_like(Q)
+    (lib().or5_prim2cons if Q.size == 5 else lib().or14_prim2cons)(Q, U)
+    return U
+
+
+def cons2prim(U):
+    U = _a(U); Q = np.empty_like(U)
+    (lib().or5_cons2prim if U.size == 5 else lib().or14_cons2prim)(U, Q)
+    return Q
+
+
+def sigma(Q):
+    Q = _a(Q)
+    return (lib().or5_sigma if Q.size == 5 else lib().or14_sigma)(Q)
+
+
+def closure5(Q, sigma_lim):
+    return lib().or5_closure(_a(Q, 5), sigma_lim)
+
+
+def closure14(Q, sigma_lim):
+    Qt = np.empty(27); Rt = np.empty(9); S = np.empty(3)
+    lib().or14_closure(_a(Q, 14), sigma_lim, Qt, Rt, S)
+    return Qt.reshape(3, 3, 3), Rt.reshape(3, 3), S
+
+
+def flux5_given_s(Q, s):
+    F = np.empty(5); lib().or5_flux_given_s(_a(Q, 5), s, F); return F
+
+
+def flux14_given_closure(Q, Qt, Rt, S, d):
+    F = np.empty(14)
+    lib().or14_flux_given_closure(_a(Q, 14), _a(np.ravel(Qt), 27), _a(np.ravel(Rt), 9),
+                                  _a(S, 3), d, F)
+    return F
+
+
+def flux(Q, sigma_lim, d=0):
+    Q = _a(Q); F = np.empty_like(Q)
+    if Q.size == 5:
+        lib().or5_flux(Q, sigma_lim, F)
+    else:
+        lib().or14_flux(Q, sigma_lim, d, F)
+    return F
+
+
+def lambda_star5(qs, sig):
+    return lib().or5_lambda_star_max(qs, sig)
+
+
+def lambda_star14(Pdd, qd, qperp, sig):
+    return lib().or14_lambda_star_max(Pdd, qd, qperp, sig)
+
+
+def wavespeeds(Q, sigma_lim, k=1.0, d=0):
+    Q = _a(Q); lo = C.c_double(); hi = C.c_double()
+    if Q.size == 5:
+        lib().or5_wavespeeds(Q, sigma_lim, k, C.byref(lo), C.byref(hi))
+    else:
+        lib().or14_wavespeeds(Q, d, sigma_lim, k, C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def source(Q, tau):
+    Q = _a(Q); Cv = np.empty_like(Q)
+    (lib().or5_source if Q.size == 5 else lib().or14_source)(Q, tau, Cv)
+    return Cv
+
+
+# ---------------------------------------------------------------- scheme API
+def make_cfg(system=14, nx=64, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, order=2,
+             integrator=RK2, flux=FLUX_HLL, limiter=LIM_MINMOD, cfl=0.5,
+             sigma_lim=1e-4, k_ws=1.0, tau_model=TAU_NONE, tau_ref=1.0, rho_ref=1.0,
+             T_ref=1.0, sides=None) -> Cfg:
+    """sides: list of 4 dicts {type, state (prim), spans: [(lo, hi, prim), ...]}."""
+    c = Cfg()
+    c.system, c.nx, c.ny = system, nx, ny
+    c.x0, c.x1, c.y0, c.y1 = x0, x1, y0, y1
+    c.order, c.integrator, c.flux, c.limiter = order, integrator, flux, limiter
+    c.cfl, c.sigma_lim, c.k_ws = cfl, sigma_lim, k_ws
+    c.tau_model, c.tau_ref, c.rho_ref, c.T_ref = tau_model, tau_ref, rho_ref, T_ref
+    sides = sides or [{} for _ in range(4)]
+    for s, sd in enumerate(sides):
+        c.side[s].base_type = sd.get("type", BC_TRANSMISSIVE)
+        st = sd.get("state")
+        if st is not None:
+            for k, v in enumerate(st):
+                c.side[s].base_state[k] = v
+        spans = sd.get("spans", [])
+        assert len(spans) <= MAX_SPANS
+        c.side[s].nspans = len(spans)
+        for n, (lo, hi, prim) in enumerate(spans):
+            c.side[s].span_lo[n] = lo
+            c.side[s].span_hi[n] = hi
+            for k, v in enumerate(prim):
+                c.side[s].span_state[n][k] = v
+    return c
+
+
+def nf_of(cfg: Cfg) -> int:
+    return 5 if cfg.system == 5 else 14
+
+
+def max_rate(cfg: Cfg, U):
+    """U: (ny, nx, nf) conserved, interior cells."""
+    return lib().or_max_rate(C.byref(cfg), _a(U).reshape(-1))
+
+
+def dt(cfg: Cfg, U, t, t_end):
+    return lib().or_dt(C.byref(cfg), _a(U).reshape(-1), t, t_end)
+
+
+def step(cfg: Cfg, U, dtv):
+    """Advance U (ny, nx, nf) by one step of size dt; returns a new array."""
+    out = np.array(U, dtype=np.float64, order="C", copy=True)
+    flat = out.reshape(-1)
+    rc = lib().or_step(C.byref(cfg), flat, dtv)
+    assert rc == 0
+    return out
+
+
+def run(cfg: Cfg, U, t, t_end, max_steps):
+    out = np.array(U, dtype=np.float64, order="C", copy=True)
+    tt = C.c_double(t)
+    hist = np.zeros(max(max_steps, 1))
+    n = lib().or_run(C.byref(cfg), out.reshape(-1), C.byref(tt), t_end, max_steps,
+                     hist.ctypes.data_as(C.c_void_p))
+    return out, tt.value, hist[:n]
+
+
+def block_step(cfg: Cfg, i0, j0, w, h, Ub, dtv):
+    """Ub: block with margins, shape (h+2My, w+2Mx, nf)."""
+    nf = nf_of(cfg)
+    out = np.empty((h, w, nf))
+    rc = lib().or_block_step(C.byref(cfg), i0, j0, w, h, _a(Ub).reshape(-1), dtv,
+                             out.reshape(-1))
+    assert rc == 0
+    return out
+
+
+def block_residual(cfg: Cfg, i0, j0, w, h, Ub):
+    nf = nf_of(cfg)
+    out = np.empty((h, w, nf))
+    lib().or_block_residual(C.byref(cfg), i0, j0, w, h, _a(Ub).reshape(-1), out.reshape(-1))
+    return out
+
+
+def tau(cfg: Cfg, Q):
+    return lib().or_tau(C.byref(cfg), _a(Q))
+
+
+def window_step(cfg: Cfg, U, i0, j0, w, h, dtv):
+    """One step of the cells [i0,i0+w) x [j0,j0+h) of the full grid U (ny,nx,nf)
+    computed on a margin-4 block cut out of U (periodic sides wrapped)."""
+    ny, nx, nf = U.shape
+    M = MARGIN
+    My = 0 if ny == 1 else M
+    per_x = cfg.side[0].base_type == BC_PERIODIC
+    per_y = ny > 1 and cfg.side[2].base_type == BC_PERIODIC
+    ii = np.arange(i0 - M, i0 + w + M)
+    jj = np.arange(j0 - My, j0 + h + My)
+    ii = np.mod(ii, nx) if per_x else np.clip(ii, 0, nx - 1)
+    jj = np.mod(jj, ny) if per_y else np.clip(jj, 0, ny - 1)
+    Ub = U[np.ix_(jj, ii)]
+    return block_step(cfg, i0, j0, w, h, Ub, dtv)
