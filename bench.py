@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: 14-moment maximum-entropy crossed supersonic jets,
+2D, midpoint RK2, MUSCL + shared minmod + HLL (Boccelli et al., JCP 2024),
+on one GB300 per rank.
+
+A step is one full RK2 step of the whole grid (two fused stage launches).
+Metric: cell-updates/s (cells x steps / s).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 4096]
+                  [--precision fp64|mixed] [--impl ours|reference]
+
+The input (4096^2 x 14 fields x 8 B = 1.9 GB per state buffer) is far larger
+than L2, so no flush is needed between timed steps.  N > 1 runs independent
+replicas, one per GPU (the method is single-grid; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s 14-mom 2D RK2 (% HBM roofline), mixed vs FP64; adjoint/fwd ratio"
+UNIT = "cell-updates/s"
+# algorithmic bytes per cell-update (each stage reads its inputs once and
+# writes its output once): FP64 stage 1 reads U^n, writes U*; stage 2 reads
+# U*, U^n, writes U^{n+1}: 5 x 14 x 8 B.
+BYTES_PER_CELL_UPDATE = {"fp64": 560.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--n", type=int, default=4096)
+    p.add_argument("--precision", default="fp64", choices=["fp64"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1])); mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local, dist
+
+
+def make_solver(mx, wl, n, precision, setup):
+    s = mx.Solver(system=14, nx=n, ny=n, precision=precision, order=2, integrator="rk2",
+                  flux="hll", limiter="minmod", cfl=0.5, sigma_lim=1e-4)
+    lo, hi = setup["slot"]
+    s.set_bc(mx.XLO, mx.BC_DIRICHLET, lo, hi, setup["left"])
+    s.set_bc(mx.YLO, mx.BC_DIRICHLET, lo, hi, setup["bottom"])
+    s.set_relaxation(mx.TAU_HARDSPHERE, setup["tau_ref"], setup["rho_ref"], setup["T_ref"])
+    return s
+
+
+def cpu_baseline(wl, seconds_target=15.0):
+    """The FP64 oracle as it stands (single thread) on a bounded sample of the
+    same workload: a 128 x 128 crossed-jets grid of the same set-up."""
+    import numpy as np
+    import oracle
+    n = 128
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(n, n, setup)
+    U = np.array([oracle.prim2cons(q) for q in prim.reshape(-1, 14)]).reshape(n, n, 14)
+    lo, hi = setup["slot"]
+    sides = [{"type": 0, "spans": [(lo, hi, setup["left"])]}, {"type": 0},
+             {"type": 0, "spans": [(lo, hi, setup["bottom"])]}, {"type": 0}]
+    cfg = oracle.make_cfg(system=14, nx=n, ny=n, tau_model=2, tau_ref=setup["tau_ref"],
+                          rho_ref=setup["rho_ref"], T_ref=setup["T_ref"], sides=sides)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        dt = oracle.dt(cfg, U, 0.0, 10.0)
+        U = oracle.step(cfg, U, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_target or steps >= 50:
+            break
+    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n}x{n} crossed jets, {steps} RK2 steps incl. CFL, {el:.1f} s, 1 thread"}
+
+
+def run_reference(args, wl):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    n = 96
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(n, n, setup)
+    U = np.array([oracle.prim2cons(q) for q in prim.reshape(-1, 14)]).reshape(n, n, 14)
+    lo, hi = setup["slot"]
+    sides = [{"type": 0, "spans": [(lo, hi, setup["left"])]}, {"type": 0},
+             {"type": 0, "spans": [(lo, hi, setup["bottom"])]}, {"type": 0}]
+    cfg = oracle.make_cfg(system=14, nx=n, ny=n, tau_model=2, tau_ref=setup["tau_ref"],
+                          rho_ref=setup["rho_ref"], T_ref=setup["T_ref"], sides=sides)
+    for _ in range(args.warmup):
+        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0))
+    el = time.perf_counter() - t0
+    v = n * n * args.steps / el
+    sample = f"{n}x{n} crossed jets per step (bounded sample of the {args.n}^2 workload), 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"crossed jets 14-moment 2D RK2, oracle sample {n}x{n}",
+                   "n": n, "precision": "fp64", "l2": "inputs larger than L2 not applicable (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_2401_15233_gb300 import workloads as wl
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    import numpy as np
+    import torch
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_2401_15233_gb300 as mx
+
+    n = args.n
+    setup = wl.jets_setup(Kn=0.1)
+    prim = np.ascontiguousarray(np.moveaxis(wl.jets_like_field(n, n, setup), -1, 0))
+    s = make_solver(mx, wl, n, args.precision, setup)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream.cuda_stream)
+    s.set_state(prim)
+    ncell = n * n
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        s.step(1, float("inf"), sync=False)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clk:
+        barrier()
+        ev[0].record(stream)
+        for k in range(args.steps):
+            s.step(1, float("inf"), sync=False)
+            ev[k + 1].record(stream)
+        barrier()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    d = s.diagnostics()
+    value = world * ncell * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C-ABI with host buffers: H2D of the state,
+    # one step, D2H of the state, every step
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(s.get_moments("conserved")).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        ne = max(2, min(args.steps, 5))
+        s.set_state(host_in.numpy(), kind="conserved")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            s.set_state(host_in.numpy(), kind="conserved")
+            s.step(1, float("inf"), sync=False)
+            s.get_moments("conserved", out=host_out.numpy())
+        el = time.perf_counter() - t0
+        nbytes = host_in.numel() * 8
+        e2e = {"value": world * ncell * ne / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ne}
+
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    bpc = BYTES_PER_CELL_UPDATE[args.precision]
+    kt = statistics.mean(per) * 1e-3        # one step = both stage launches of the kernel
+    achieved = bpc * ncell / kt / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
+                   "n": n, "precision": args.precision, "flux": "hll", "limiter": "minmod",
+                   "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "mxe_stage14_2d_f64", "peak_source": src,
+                     "bytes_per_cell_update": bpc},
+        "gpu_launches": 2 * args.steps,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "diag": {"t": d["t"], "steps": d["steps"], "min_sigma": d["min_sigma"],
+                 "n_sigma_below_lim": d["n_sigma_below_lim"], "n_nonfinite": d["n_nonfinite"]},
+    }
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

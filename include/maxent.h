@@ -1,0 +1,191 @@
+/*
+ * maxent.h -- C-ABI of the GB300 (sm_103a) maximum-entropy moment solver.
+ *
+ * The library advances the 5-moment (1D1V) and 14-moment (3D3V) fourth-order
+ * maximum-entropy systems with the interpolative closure of McDonald &
+ * Torrilhon, as used by Boccelli, Kaufmann, Magin & McDonald (JCP 2024,
+ * arXiv 2401.15233), with an explicit cell-centred finite-volume scheme:
+ * MUSCL reconstruction of primitive moments with one shared limiter
+ * (Sec. 3.2), HLL or Rusanov face fluxes (Sec. 3.1) with the approximate
+ * wave speeds of Sec. 5 / Appendix B, BGK relaxation sources (Sec. 2.3,
+ * 2.4), forward Euler or midpoint RK2 in time (Sec. 3) under a CFL condition.
+ *
+ * The calls follow the paper's statement of the problem: an initial state,
+ * boundary states imposed in ghost cells (Sec. 6), a relaxation time
+ * (Sec. 2.1, Sec. 4), time marching, and moments read back.
+ *
+ * Ownership and threading
+ *   - A context owns all device memory it allocates; mxe_destroy frees it.
+ *   - Pointers passed in are borrowed for the duration of the call only.
+ *   - Work is issued on the context's CUDA stream (mxe_set_stream); calls
+ *     that return host data synchronise that stream.  A context must not be
+ *     used from two host threads at once.
+ *   - Every call returns an mxe_status; MXE_OK is 0.  On error the context's
+ *     message (mxe_last_error) says what failed; no call aborts the process.
+ *
+ * Array layouts (double precision, structure of arrays)
+ *   2D grid:  soa[k * ny * nx + j * nx + i], k = field, j = row (y), i = column (x)
+ *   1D tubes: fields of tube n follow each other: soa[k * ncells_n + i],
+ *             tubes concatenated in order (mxe_batch_* calls).
+ *   5-moment primitive fields : (rho, u, P, q, r)                  Sec. 2.3
+ *   14-moment primitive fields: (rho, ux, uy, uz, Pxx, Pxy, Pxz, Pyy, Pyz,
+ *                                Pzz, qx, qy, qz, R)                Sec. 2.4
+ *   q is the full third central moment (q_i = Q_ijj, twice the fluid heat
+ *   flux, Sec. 2.1).  Conserved fields are the balance-law densities.
+ */
+#ifndef MAXENT_H
+#define MAXENT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MXE_OK = 0,
+    MXE_EINVAL = 1,          /* bad argument (size, enum, pointer, range)      */
+    MXE_ENOMEM = 2,          /* device or host allocation failed               */
+    MXE_ECUDA = 3,           /* a CUDA runtime call failed                     */
+    MXE_EUNREALIZABLE = 4,   /* input state not realizable (rho<=0, P not SPD,
+                                sigma > 1)                                     */
+    MXE_ENONFINITE = 5,      /* a non-finite value appeared in the state       */
+    MXE_ETIMEOUT = 6,        /* a bounded device wait gave up                  */
+    MXE_ESTATE = 7           /* call not valid in the context's current state  */
+} mxe_status;
+
+enum { MXE_FP64 = 0, MXE_MIXED = 1 };                 /* precision            */
+enum { MXE_FLUX_HLL = 0, MXE_FLUX_RUSANOV = 1 };      /* Sec. 3.1             */
+enum { MXE_LIM_MINMOD = 0, MXE_LIM_VANALBADA = 1 };   /* Sec. 3.2             */
+enum { MXE_FE = 0, MXE_RK2 = 1 };                     /* Sec. 3               */
+enum { MXE_BC_TRANSMISSIVE = 0, MXE_BC_PERIODIC = 1, MXE_BC_DIRICHLET = 2 };
+enum { MXE_SIDE_XLO = 0, MXE_SIDE_XHI = 1, MXE_SIDE_YLO = 2, MXE_SIDE_YHI = 3 };
+enum { MXE_TAU_NONE = 0, MXE_TAU_CONST = 1, MXE_TAU_HARDSPHERE = 2 };
+enum { MXE_PRIMITIVE = 0, MXE_CONSERVED = 1, MXE_SIGMA = 2 };
+
+typedef struct {
+    int    system;       /* 5 (1D1V, Sec. 2.3) or 14 (3D3V, Sec. 2.4)            */
+    int    nx, ny;       /* cells; ny == 1 means one space dimension (x)          */
+    double x0, x1, y0, y1;                    /* domain                            */
+    int    precision;    /* MXE_FP64 or MXE_MIXED (FP32 stage arithmetic, FP64
+                            state accumulator and FP64 closure near sigma -> 0 or
+                            sigma -> 1)                                         */
+    int    flux;         /* MXE_FLUX_*                                            */
+    int    limiter;      /* MXE_LIM_* (shared most-stringent limiter, Sec. 3.2)   */
+    int    order;        /* 1 (piecewise constant) or 2 (MUSCL)                   */
+    int    integrator;   /* MXE_FE or MXE_RK2 (midpoint)                          */
+    double cfl;          /* Courant number (0.5 in Sec. 6)                        */
+    double sigma_lim;    /* lower bound on sigma inside closure and wave speeds
+                            (Appendix A; 1e-4 in the paper)                      */
+    double k_ws;         /* wave-speed inflation k >= 1 (Sec. 5.1)                */
+} mxe_config;
+
+typedef struct {
+    double    t;                /* simulated time                                  */
+    double    last_dt;          /* last time step taken                            */
+    long long steps;            /* steps taken since mxe_set_state                 */
+    double    max_rate;         /* CFL denominator sum_d max|lambda_d|/dx_d        */
+    double    min_sigma;        /* minimum raw sigma over cells (14- or 5-moment)  */
+    long long n_sigma_below_lim;/* cells with sigma < sigma_lim                    */
+    long long n_sigma_above_one;/* cells with sigma > 1 (unrealizable)             */
+    long long n_nonpositive;    /* cells with rho <= 0 or a non-positive pressure  */
+    long long n_nonfinite;      /* cells with a non-finite conserved value         */
+    long long n_fp64_closures;  /* MIXED: face states evaluated in FP64 (last step)*/
+    long long n_closures;       /* MIXED: face states evaluated in total (last step)*/
+    double    sums[14];         /* sum over cells of each conserved field          */
+} mxe_diag;
+
+typedef struct mxe_ctx mxe_ctx;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a solver for one grid (ny >= 1).  Validates the configuration
+ * (system in {5,14}; 5-moment requires ny == 1; nx >= 4; cfl > 0;
+ * 0 <= sigma_lim < 1; k_ws >= 1) and allocates the device state.
+ * Default BCs: transmissive on every side; default relaxation: none. */
+mxe_status mxe_create(const mxe_config *cfg, mxe_ctx **out);
+
+/* Free all device memory of the context.  NULL is allowed. */
+void mxe_destroy(mxe_ctx *ctx);
+
+/* Issue all further work on `stream` (a cudaStream_t; NULL = the context's
+ * own non-blocking stream).  The stream is borrowed, not owned. */
+mxe_status mxe_set_stream(mxe_ctx *ctx, void *stream);
+void      *mxe_get_stream(const mxe_ctx *ctx);
+
+/* Set the state from a SoA array of nf*ny*nx doubles (kind PRIMITIVE or
+ * CONSERVED; primitives are converted on the device).  on_device != 0: soa
+ * is a device pointer.  Resets t = 0 and the step count.  Every cell is
+ * checked (rho > 0, finite, positive pressure); a failing state returns
+ * MXE_EUNREALIZABLE with the first offending cell in the message and
+ * leaves the previous state in place. */
+mxe_status mxe_set_state(mxe_ctx *ctx, int kind, const double *soa, int on_device);
+
+/* Read the state into a SoA array (kind PRIMITIVE, CONSERVED; or SIGMA: one
+ * field, the raw sigma of Eq. (sigma-mapping-5mom/14mom)).  Synchronises. */
+mxe_status mxe_get_moments(mxe_ctx *ctx, int kind, double *soa, int on_device);
+
+/* Boundary condition of one side (Sec. 6: states imposed in two ghost
+ * layers).  type TRANSMISSIVE copies the nearest interior cell, PERIODIC
+ * wraps (must be set on both opposite sides), DIRICHLET imposes the
+ * primitive state `prim` (nf values).  With lo < hi and type DIRICHLET the
+ * state is imposed only on ghost cells whose tangential centre coordinate
+ * lies in [lo, hi] (an inflow slot); up to 4 slots per side, the rest of
+ * the side keeps its base type.  lo >= hi sets the base type of the side
+ * and clears its slots. */
+mxe_status mxe_set_bc(mxe_ctx *ctx, int side, int type, double lo, double hi,
+                      const double *prim);
+
+/* Relaxation time of the BGK source (Sec. 2.1, Sec. 4):
+ *   NONE       collisionless (no source)
+ *   CONST      tau = tau_ref everywhere
+ *   HARDSPHERE tau = tau_ref (rho_ref/rho) sqrt(T_ref/T), T = P/rho (1D1V) or
+ *              tr(P)/(3 rho) (3D3V); with tau_ref = Kn L_ref / sqrt(8 T_ref/pi)
+ *              this is lambda/v_th with lambda proportional to 1/rho. */
+mxe_status mxe_set_relaxation(mxe_ctx *ctx, int model, double tau_ref, double rho_ref,
+                              double T_ref);
+
+/* March until t_end or max_steps steps, with dt = min(cfl/max_rate, t_end-t)
+ * recomputed every step on the device.  t_out / steps_out (may be NULL)
+ * receive the new time and the steps taken in this call; passing either
+ * synchronises.  Returns MXE_ENONFINITE if a non-finite value appeared. */
+mxe_status mxe_step(mxe_ctx *ctx, int max_steps, double t_end, double *t_out,
+                    int *steps_out);
+
+/* Take n steps with prescribed time steps dts[0..n-1] (host array) instead
+ * of the CFL value (e.g. a recorded sequence). */
+mxe_status mxe_step_dt(mxe_ctx *ctx, int n, const double *dts);
+
+/* Diagnostics of the current state (synchronises).  dt_hist (may be NULL,
+ * capacity n) receives the most recent time steps, oldest first. */
+mxe_status mxe_get_diagnostics(mxe_ctx *ctx, mxe_diag *out);
+
+/* Last error message of the context (never NULL; "" if none). */
+const char *mxe_last_error(const mxe_ctx *ctx);
+
+/* ---- batched 1D tubes ---------------------------------------------------- */
+
+/* Create n independent 1D problems (cfg->ny must be 1; cfg->nx is ignored):
+ * tube b has ncells[b] cells on [0, length[b]].  All tubes share system,
+ * precision, scheme and CFL; each has its own state, BCs (transmissive by
+ * default), relaxation time and clock.  mxe_set_state / mxe_get_moments act
+ * on the concatenation of all tubes.  The whole batch advances in one
+ * persistent launch (one thread block or cluster per tube). */
+mxe_status mxe_batch_create(const mxe_config *cfg, int n, const int *ncells,
+                            const double *length, mxe_ctx **out);
+
+/* Per-tube relaxation (same models as mxe_set_relaxation). */
+mxe_status mxe_batch_set_relaxation(mxe_ctx *ctx, int tube, int model, double tau_ref,
+                                    double rho_ref, double T_ref);
+
+/* Per-tube times and step counts (host arrays of n, may be NULL). */
+mxe_status mxe_batch_get_clock(mxe_ctx *ctx, double *t, long long *steps);
+
+/* Advance every tube until its own t reaches t_end or it has taken
+ * max_steps steps in this call; one launch for the whole batch. */
+mxe_status mxe_batch_run(mxe_ctx *ctx, int max_steps, double t_end);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

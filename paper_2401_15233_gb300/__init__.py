@@ -1,0 +1,331 @@
+"""GB300-native solver for the fourth-order maximum-entropy moment method with
+interpolative closure (Boccelli, Kaufmann, Magin & McDonald, JCP 2024).
+
+This module is a thin ctypes binding of the C-ABI in ``include/maxent.h``
+(library ``_lib/libmaxent.so``, CUDA for sm_103a).  It only marshals
+arguments: every step of the method runs in the library's CUDA kernels.
+The module-level functions carry the C names; ``Solver`` and ``Batch`` wrap
+them for convenience.  Arrays are structure-of-arrays float64:
+``(nf, ny, nx)`` for grids and the concatenation of ``(nf, ncells_b)`` for
+batched tubes.  torch CUDA tensors are passed by device pointer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "Config", "Diag", "Solver", "Batch", "MaxentError", "lib",
+    "mxe_create", "mxe_destroy", "mxe_set_stream", "mxe_get_stream", "mxe_set_state",
+    "mxe_get_moments", "mxe_set_bc", "mxe_set_relaxation", "mxe_step", "mxe_step_dt",
+    "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
+    "mxe_batch_get_clock", "mxe_batch_run",
+]
+
+OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
+FP64, MIXED = 0, 1
+FLUX_HLL, FLUX_RUSANOV = 0, 1
+LIM_MINMOD, LIM_VANALBADA = 0, 1
+FE, RK2 = 0, 1
+BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
+XLO, XHI, YLO, YHI = 0, 1, 2, 3
+TAU_NONE, TAU_CONST, TAU_HARDSPHERE = 0, 1, 2
+PRIMITIVE, CONSERVED, SIGMA = 0, 1, 2
+_KINDS = {"primitive": PRIMITIVE, "conserved": CONSERVED, "sigma": SIGMA}
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("system", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+        ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+        ("precision", C.c_int), ("flux", C.c_int), ("limiter", C.c_int),
+        ("order", C.c_int), ("integrator", C.c_int),
+        ("cfl", C.c_double), ("sigma_lim", C.c_double), ("k_ws", C.c_double),
+    ]
+
+
+class Diag(C.Structure):
+    _fields_ = [
+        ("t", C.c_double), ("last_dt", C.c_double), ("steps", C.c_longlong),
+        ("max_rate", C.c_double), ("min_sigma", C.c_double),
+        ("n_sigma_below_lim", C.c_longlong), ("n_sigma_above_one", C.c_longlong),
+        ("n_nonpositive", C.c_longlong), ("n_nonfinite", C.c_longlong),
+        ("n_fp64_closures", C.c_longlong), ("n_closures", C.c_longlong),
+        ("sums", C.c_double * 14),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "sums"}
+        d["sums"] = list(self.sums)
+        return d
+
+
+class MaxentError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"maxent status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def lib():
+    """Load libmaxent.so (building it first if sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        sig = {
+            "mxe_create": ([C.POINTER(Config), C.POINTER(_P)], C.c_int),
+            "mxe_destroy": ([_P], None),
+            "mxe_set_stream": ([_P, _P], C.c_int),
+            "mxe_get_stream": ([_P], _P),
+            "mxe_set_state": ([_P, C.c_int, _P, C.c_int], C.c_int),
+            "mxe_get_moments": ([_P, C.c_int, _P, C.c_int], C.c_int),
+            "mxe_set_bc": ([_P, C.c_int, C.c_int, C.c_double, C.c_double, _P], C.c_int),
+            "mxe_set_relaxation": ([_P, C.c_int, C.c_double, C.c_double, C.c_double], C.c_int),
+            "mxe_step": ([_P, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int)],
+                         C.c_int),
+            "mxe_step_dt": ([_P, C.c_int, _P], C.c_int),
+            "mxe_get_diagnostics": ([_P, C.POINTER(Diag)], C.c_int),
+            "mxe_last_error": ([_P], C.c_char_p),
+            "mxe_batch_create": ([C.POINTER(Config), C.c_int, _P, _P, C.POINTER(_P)], C.c_int),
+            "mxe_batch_set_relaxation": ([_P, C.c_int, C.c_int, C.c_double, C.c_double,
+                                          C.c_double], C.c_int),
+            "mxe_batch_get_clock": ([_P, _P, _P], C.c_int),
+            "mxe_batch_run": ([_P, C.c_int, C.c_double], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != OK:
+        msg = lib().mxe_last_error(ctx).decode() if ctx else ""
+        raise MaxentError(st, msg)
+
+
+def _ptr(a, nbytes=None):
+    """(pointer, on_device) of a numpy array or a CUDA tensor (float64, contiguous)."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous float64")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+# ------------------------------------------------------------ C-named wrappers
+def mxe_create(cfg: Config):
+    h = _P()
+    st = lib().mxe_create(C.byref(cfg), C.byref(h))
+    if st != OK:
+        raise MaxentError(st, "mxe_create rejected the configuration")
+    return h
+
+
+def mxe_destroy(ctx):
+    lib().mxe_destroy(ctx)
+
+
+def mxe_set_stream(ctx, stream_ptr):
+    _check(ctx, lib().mxe_set_stream(ctx, _P(stream_ptr)))
+
+
+def mxe_get_stream(ctx):
+    return lib().mxe_get_stream(ctx)
+
+
+def mxe_set_state(ctx, kind, arr):
+    p, dev = _ptr(arr)
+    _check(ctx, lib().mxe_set_state(ctx, kind, p, dev))
+
+
+def mxe_get_moments(ctx, kind, out):
+    p, dev = _ptr(out)
+    _check(ctx, lib().mxe_get_moments(ctx, kind, p, dev))
+    return out
+
+
+def mxe_set_bc(ctx, side, bctype, lo=0.0, hi=0.0, prim=None):
+    buf = None
+    if prim is not None:
+        buf = np.ascontiguousarray(np.asarray(prim, dtype=np.float64))
+    _check(ctx, lib().mxe_set_bc(ctx, side, bctype, lo, hi,
+                                 _P(buf.ctypes.data) if buf is not None else None))
+
+
+def mxe_set_relaxation(ctx, model, tau_ref=1.0, rho_ref=1.0, T_ref=1.0):
+    _check(ctx, lib().mxe_set_relaxation(ctx, model, tau_ref, rho_ref, T_ref))
+
+
+def mxe_step(ctx, max_steps, t_end, sync=True):
+    if not sync:
+        _check(ctx, lib().mxe_step(ctx, max_steps, t_end, None, None))
+        return None
+    t = C.c_double()
+    n = C.c_int()
+    _check(ctx, lib().mxe_step(ctx, max_steps, t_end, C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def mxe_step_dt(ctx, dts):
+    d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    _check(ctx, lib().mxe_step_dt(ctx, d.size, _P(d.ctypes.data)))
+
+
+def mxe_get_diagnostics(ctx):
+    d = Diag()
+    _check(ctx, lib().mxe_get_diagnostics(ctx, C.byref(d)))
+    return d.as_dict()
+
+
+def mxe_last_error(ctx):
+    return lib().mxe_last_error(ctx).decode()
+
+
+def mxe_batch_create(cfg: Config, ncells, lengths):
+    nc = np.ascontiguousarray(np.asarray(ncells, dtype=np.int32))
+    ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.float64))
+    h = _P()
+    st = lib().mxe_batch_create(C.byref(cfg), nc.size, _P(nc.ctypes.data), _P(ln.ctypes.data),
+                                C.byref(h))
+    if st != OK:
+        raise MaxentError(st, "mxe_batch_create rejected the configuration")
+    return h
+
+
+def mxe_batch_set_relaxation(ctx, tube, model, tau_ref=1.0, rho_ref=1.0, T_ref=1.0):
+    _check(ctx, lib().mxe_batch_set_relaxation(ctx, tube, model, tau_ref, rho_ref, T_ref))
+
+
+def mxe_batch_get_clock(ctx, n):
+    t = np.zeros(n)
+    s = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().mxe_batch_get_clock(ctx, _P(t.ctypes.data), _P(s.ctypes.data)))
+    return t, s
+
+
+def mxe_batch_run(ctx, max_steps, t_end):
+    _check(ctx, lib().mxe_batch_run(ctx, max_steps, t_end))
+
+
+# ------------------------------------------------------------ convenience
+_ENUM = {
+    "fp64": FP64, "mixed": MIXED, "hll": FLUX_HLL, "rusanov": FLUX_RUSANOV,
+    "minmod": LIM_MINMOD, "vanalbada": LIM_VANALBADA, "fe": FE, "rk2": RK2,
+}
+
+
+def make_config(system=14, nx=64, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, precision="fp64",
+                flux="hll", limiter="minmod", order=2, integrator="rk2", cfl=0.5,
+                sigma_lim=1e-4, k_ws=1.0) -> Config:
+    e = lambda v: _ENUM[v] if isinstance(v, str) else int(v)
+    return Config(system, nx, ny, x0, x1, y0, y1, e(precision), e(flux), e(limiter), order,
+                  e(integrator), cfl, sigma_lim, k_ws)
+
+
+class Solver:
+    """One grid (ny == 1: a single 1D problem)."""
+
+    def __init__(self, **kw):
+        self.cfg = make_config(**kw)
+        self.nf = self.cfg.system
+        self.ctx = mxe_create(self.cfg)
+        self.shape = (self.nf, self.cfg.ny, self.cfg.nx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mxe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        mxe_set_stream(self.ctx, stream_ptr)
+
+    @property
+    def stream(self):
+        return mxe_get_stream(self.ctx)
+
+    def set_state(self, arr, kind="primitive"):
+        if isinstance(arr, np.ndarray):
+            arr = np.ascontiguousarray(arr, dtype=np.float64)
+        mxe_set_state(self.ctx, _KINDS[kind], arr)
+
+    def get_moments(self, kind="primitive", out=None):
+        if out is None:
+            shape = (1,) + self.shape[1:] if kind == "sigma" else self.shape
+            out = np.empty(shape)
+        return mxe_get_moments(self.ctx, _KINDS[kind], out)
+
+    def set_bc(self, side, bctype, lo=0.0, hi=0.0, state=None):
+        mxe_set_bc(self.ctx, side, bctype, lo, hi, state)
+
+    def set_relaxation(self, model, tau_ref=1.0, rho_ref=1.0, T_ref=1.0):
+        mxe_set_relaxation(self.ctx, model, tau_ref, rho_ref, T_ref)
+
+    def step(self, max_steps, t_end=float("inf"), sync=True):
+        return mxe_step(self.ctx, max_steps, t_end, sync)
+
+    def step_dt(self, dts):
+        mxe_step_dt(self.ctx, dts)
+
+    def diagnostics(self):
+        return mxe_get_diagnostics(self.ctx)
+
+
+class Batch(Solver):
+    """Independent 1D tubes advanced in one persistent launch."""
+
+    def __init__(self, ncells, lengths, **kw):
+        kw.setdefault("ny", 1)
+        kw["nx"] = int(max(ncells))
+        self.cfg = make_config(**kw)
+        self.nf = self.cfg.system
+        self.ncells = [int(n) for n in ncells]
+        self.ctx = mxe_batch_create(self.cfg, self.ncells, lengths)
+        self.shape = (self.nf * sum(self.ncells),)
+
+    def pack(self, tubes):
+        """list of (nf, n_b) arrays -> concatenated SoA"""
+        return np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).ravel()
+                                                    for t in tubes]))
+
+    def unpack(self, flat, nf=None):
+        nf = nf or self.nf
+        out, o = [], 0
+        for n in self.ncells:
+            out.append(flat[o:o + nf * n].reshape(nf, n))
+            o += nf * n
+        return out
+
+    def get_moments(self, kind="primitive", out=None):
+        if out is None:
+            out = np.empty(sum(self.ncells) if kind == "sigma" else self.shape)
+        return mxe_get_moments(self.ctx, _KINDS[kind], out)
+
+    def set_tube_relaxation(self, tube, model, tau_ref=1.0, rho_ref=1.0, T_ref=1.0):
+        mxe_batch_set_relaxation(self.ctx, tube, model, tau_ref, rho_ref, T_ref)
+
+    def clock(self):
+        return mxe_batch_get_clock(self.ctx, len(self.ncells))
+
+    def run(self, max_steps, t_end):
+        mxe_batch_run(self.ctx, max_steps, t_end)

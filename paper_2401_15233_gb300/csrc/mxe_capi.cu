@@ -1,0 +1,731 @@
+// mxe_capi.cu -- host implementation of the C-ABI declared in include/maxent.h.
+//
+// A context owns its device buffers and a CUDA stream.  2D grids advance
+// with one fused tile kernel per RK stage (dt formed on the device from the
+// previous step's CFL reduction, so a step needs no host round trip); 1D
+// problems and batches of tubes advance inside one persistent launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/maxent.h"
+#include "mxe_internal.h"
+
+namespace mxe {
+// kernels defined in the other translation units
+extern "C" __global__ void mxe_stage14_2d_f64(const Stage2DArgs a);
+extern "C" __global__ void mxe_rate14_2d(const double* U, Grid2D g, SchemeParams sp,
+                                         DevClock* clk, int slot);
+extern "C" __global__ void mxe_tubes5_f64(const TubeArgs a);
+extern "C" __global__ void mxe_tubes14_f64(const TubeArgs a);
+size_t stage14_2d_f64_smem();
+int tile_x();
+int tile_y();
+int tubes_threads();
+
+extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
+                                          unsigned long long* bad);
+extern "C" __global__ void mxe_k_setstate(CellMap m, int nf, int kind, const double* src,
+                                          double* U);
+extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const double* U,
+                                          double* dst);
+extern "C" __global__ void mxe_k_ghost(int nf, int n, const double* in, double* out);
+extern "C" __global__ void mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim,
+                                      double* acc, unsigned long long* cnt);
+}  // namespace mxe
+
+using namespace mxe;
+
+struct mxe_ctx {
+    mxe_config cfg;
+    int nf = 14;
+    bool tubes = false;               // 1D problems (single or batched)
+    int ntubes = 0;
+    long long ncell = 0;              // cells in total
+    long long nelem = 0;              // device elements per state buffer
+    // 2D grid
+    Grid2D g{};
+    int slot = 0;
+    DevClock* clk = nullptr;
+    // tubes
+    std::vector<TubeDesc> tdesc;
+    std::vector<int> tn;
+    TubeDesc* tdesc_d = nullptr;
+    TubeClock* tclk = nullptr;
+    // state
+    double* U = nullptr;
+    double* Us = nullptr;
+    double* stage = nullptr;          // dense staging buffer (nf * ncell)
+    double* dts_d = nullptr;          // prescribed dt sequence
+    int dts_cap = 0;
+    unsigned long long* scratch = nullptr;  // validation / diagnostics counters
+    double* accd = nullptr;
+    // boundary conditions
+    int bc_type[4] = {0, 0, 0, 0};
+    int nspans[4] = {0, 0, 0, 0};
+    double span_lo[4][MAX_SPANS], span_hi[4][MAX_SPANS];
+    double ghost_h[4][GHOST_SLOTS][14];
+    double* ghost_in = nullptr;       // raw prim states (device)
+    double* ghost_d = nullptr;        // round-tripped (device)
+    RelaxParams rp{0, 1.0, 1.0, 1.0};
+    SchemeParams sp{};
+    bool have_state = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    std::string err;
+};
+
+static mxe_status fail(mxe_ctx* c, mxe_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(c, MXE_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+static CellMap cellmap(const mxe_ctx* c) {
+    CellMap m{};
+    m.nf = c->nf;
+    if (c->tubes) {
+        m.mode = 1;
+        m.tubes = c->tdesc_d;
+        m.ntubes = c->ntubes;
+    } else {
+        m.mode = 0;
+        m.nx = c->g.nx;
+        m.ny = c->g.ny;
+        m.pitch = c->g.pitch;
+        m.fstride = c->g.fstride;
+    }
+    return m;
+}
+
+static dim3 cellgrid(const mxe_ctx* c, int threads) {
+    if (c->tubes) {
+        int mx = *std::max_element(c->tn.begin(), c->tn.end());
+        return dim3((mx + threads - 1) / threads, c->ntubes);
+    }
+    return dim3((c->g.nx + threads - 1) / threads, c->g.ny);
+}
+
+static mxe_status check_cfg(mxe_ctx* c, const mxe_config* cfg, bool batch) {
+    if (!cfg) return fail(c, MXE_EINVAL, "cfg is NULL");
+    if (cfg->system != 5 && cfg->system != 14)
+        return fail(c, MXE_EINVAL, "system must be 5 or 14 (got %d)", cfg->system);
+    if (!batch) {
+        if (cfg->nx < 4 || cfg->ny < 1) return fail(c, MXE_EINVAL, "need nx >= 4 and ny >= 1");
+        if (cfg->ny > 1 && cfg->ny < 4) return fail(c, MXE_EINVAL, "2D grids need ny >= 4");
+        if (!(cfg->x1 > cfg->x0)) return fail(c, MXE_EINVAL, "need x1 > x0");
+        if (cfg->ny > 1 && !(cfg->y1 > cfg->y0)) return fail(c, MXE_EINVAL, "need y1 > y0");
+    }
+    if (cfg->system == 5 && cfg->ny != 1)
+        return fail(c, MXE_EINVAL, "the 5-moment (1D1V) system needs ny == 1");
+    if (cfg->precision != MXE_FP64 && cfg->precision != MXE_MIXED)
+        return fail(c, MXE_EINVAL, "precision must be MXE_FP64 or MXE_MIXED");
+    if (cfg->precision == MXE_MIXED)
+        return fail(c, MXE_EINVAL, "MXE_MIXED is not available in this build");
+    if (cfg->flux != MXE_FLUX_HLL && cfg->flux != MXE_FLUX_RUSANOV)
+        return fail(c, MXE_EINVAL, "unknown flux %d", cfg->flux);
+    if (cfg->limiter != MXE_LIM_MINMOD && cfg->limiter != MXE_LIM_VANALBADA)
+        return fail(c, MXE_EINVAL, "unknown limiter %d", cfg->limiter);
+    if (cfg->order != 1 && cfg->order != 2) return fail(c, MXE_EINVAL, "order must be 1 or 2");
+    if (cfg->integrator != MXE_FE && cfg->integrator != MXE_RK2)
+        return fail(c, MXE_EINVAL, "integrator must be MXE_FE or MXE_RK2");
+    if (!(cfg->cfl > 0.0)) return fail(c, MXE_EINVAL, "cfl must be > 0");
+    if (!(cfg->sigma_lim > 0.0 && cfg->sigma_lim < 1.0))
+        return fail(c, MXE_EINVAL, "sigma_lim must lie in (0, 1)");
+    if (!(cfg->k_ws >= 1.0)) return fail(c, MXE_EINVAL, "k_ws must be >= 1");
+    return MXE_OK;
+}
+
+static mxe_status alloc_common(mxe_ctx* c) {
+    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    CK(cudaMalloc(&c->U, sizeof(double) * c->nelem));
+    CK(cudaMalloc(&c->Us, sizeof(double) * c->nelem));
+    CK(cudaMemset(c->U, 0, sizeof(double) * c->nelem));
+    CK(cudaMemset(c->Us, 0, sizeof(double) * c->nelem));
+    CK(cudaMalloc(&c->stage, sizeof(double) * c->nf * c->ncell));
+    CK(cudaMalloc(&c->scratch, sizeof(unsigned long long) * 8));
+    CK(cudaMalloc(&c->accd, sizeof(double) * 32));
+    CK(cudaMalloc(&c->ghost_in, sizeof(double) * 4 * GHOST_SLOTS * 14));
+    CK(cudaMalloc(&c->ghost_d, sizeof(double) * 4 * GHOST_SLOTS * 14));
+    memset(c->ghost_h, 0, sizeof c->ghost_h);
+    CK(cudaMemset(c->ghost_d, 0, sizeof(double) * 4 * GHOST_SLOTS * 14));
+    c->sp.sigma_lim = c->cfg.sigma_lim;
+    c->sp.k_ws = c->cfg.k_ws;
+    c->sp.flux = c->cfg.flux;
+    c->sp.limiter = c->cfg.limiter;
+    c->sp.order = c->cfg.order;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
+    if (!out) return MXE_EINVAL;
+    *out = nullptr;
+    mxe_ctx* c = new (std::nothrow) mxe_ctx();
+    if (!c) return MXE_ENOMEM;
+    mxe_status s = check_cfg(c, cfg, false);
+    if (s != MXE_OK) {
+        delete c;
+        return s;
+    }
+    c->cfg = *cfg;
+    c->nf = cfg->system;
+    if (cfg->ny == 1) {                 // 1D: a batch of one tube
+        c->tubes = true;
+        c->ntubes = 1;
+        TubeDesc td{};
+        td.off = 0;
+        td.n = cfg->nx;
+        td.dx = (cfg->x1 - cfg->x0) / cfg->nx;
+        td.rp = c->rp;
+        c->tdesc.push_back(td);
+        c->tn.push_back(cfg->nx);
+        c->ncell = cfg->nx;
+        c->nelem = (long long)c->nf * cfg->nx;
+    } else {
+        c->g.nx = cfg->nx;
+        c->g.ny = cfg->ny;
+        c->g.pitch = (cfg->nx + 31) / 32 * 32;
+        c->g.fstride = (long long)c->g.pitch * cfg->ny;
+        c->g.dx = (cfg->x1 - cfg->x0) / cfg->nx;
+        c->g.dy = (cfg->y1 - cfg->y0) / cfg->ny;
+        c->ncell = (long long)cfg->nx * cfg->ny;
+        c->nelem = (long long)c->nf * c->g.fstride;
+    }
+    s = alloc_common(c);
+    if (s == MXE_OK && c->tubes) {
+        cudaError_t e = cudaMalloc(&c->tdesc_d, sizeof(TubeDesc) * c->ntubes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->tclk, sizeof(TubeClock) * c->ntubes);
+        if (e == cudaSuccess) e = cudaMemset(c->tclk, 0, sizeof(TubeClock) * c->ntubes);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * c->ntubes,
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(c, MXE_ECUDA, "tube set-up: %s", cudaGetErrorString(e));
+    } else if (s == MXE_OK) {
+        cudaError_t e = cudaMalloc(&c->clk, sizeof(DevClock));
+        if (e == cudaSuccess) e = cudaMemset(c->clk, 0, sizeof(DevClock));
+        if (e != cudaSuccess) s = fail(c, MXE_ECUDA, "clock: %s", cudaGetErrorString(e));
+    }
+    if (s != MXE_OK) {
+        mxe_destroy(c);
+        return s;
+    }
+    c->g.ghost = c->ghost_d;
+    if (!c->tubes) {
+        cudaError_t e = cudaFuncSetAttribute(mxe_stage14_2d_f64,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)stage14_2d_f64_smem());
+        if (e != cudaSuccess) {
+            fail(c, MXE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
+            mxe_destroy(c);
+            return MXE_ECUDA;
+        }
+    }
+    *out = c;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_create(const mxe_config* cfg, int n, const int* ncells,
+                                       const double* length, mxe_ctx** out) {
+    if (!out) return MXE_EINVAL;
+    *out = nullptr;
+    mxe_ctx* c = new (std::nothrow) mxe_ctx();
+    if (!c) return MXE_ENOMEM;
+    mxe_status s = check_cfg(c, cfg, true);
+    if (s == MXE_OK && cfg->ny != 1) s = fail(c, MXE_EINVAL, "batched tubes need ny == 1");
+    if (s == MXE_OK && (n < 1 || !ncells || !length)) s = fail(c, MXE_EINVAL, "bad tube list");
+    if (s != MXE_OK) {
+        delete c;
+        return s;
+    }
+    c->cfg = *cfg;
+    c->nf = cfg->system;
+    c->tubes = true;
+    c->ntubes = n;
+    long long off = 0;
+    for (int b = 0; b < n; ++b) {
+        if (ncells[b] < 4 || !(length[b] > 0.0)) {
+            delete c;
+            return MXE_EINVAL;
+        }
+        TubeDesc td{};
+        td.off = off;
+        td.n = ncells[b];
+        td.dx = length[b] / ncells[b];
+        td.rp = c->rp;
+        c->tdesc.push_back(td);
+        c->tn.push_back(ncells[b]);
+        off += (long long)c->nf * ncells[b];
+        c->ncell += ncells[b];
+    }
+    c->nelem = off;
+    s = alloc_common(c);
+    if (s == MXE_OK) {
+        cudaError_t e = cudaMalloc(&c->tdesc_d, sizeof(TubeDesc) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->tclk, sizeof(TubeClock) * n);
+        if (e == cudaSuccess) e = cudaMemset(c->tclk, 0, sizeof(TubeClock) * n);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * n,
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(c, MXE_ECUDA, "tube set-up: %s", cudaGetErrorString(e));
+    }
+    if (s != MXE_OK) {
+        mxe_destroy(c);
+        return s;
+    }
+    *out = c;
+    return MXE_OK;
+}
+
+extern "C" void mxe_destroy(mxe_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->U);
+    cudaFree(c->Us);
+    cudaFree(c->stage);
+    cudaFree(c->scratch);
+    cudaFree(c->accd);
+    cudaFree(c->ghost_in);
+    cudaFree(c->ghost_d);
+    cudaFree(c->clk);
+    cudaFree(c->tdesc_d);
+    cudaFree(c->tclk);
+    cudaFree(c->dts_d);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+extern "C" mxe_status mxe_set_stream(mxe_ctx* c, void* stream) {
+    if (!c) return MXE_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+    return MXE_OK;
+}
+
+extern "C" void* mxe_get_stream(const mxe_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+extern "C" const char* mxe_last_error(const mxe_ctx* c) { return c ? c->err.c_str() : ""; }
+
+// ---------------------------------------------------------------- clocks
+static mxe_status reset_clock(mxe_ctx* c) {
+    if (c->tubes) {
+        std::vector<TubeClock> z(c->ntubes);
+        memset(z.data(), 0, sizeof(TubeClock) * c->ntubes);
+        CK(cudaMemcpyAsync(c->tclk, z.data(), sizeof(TubeClock) * c->ntubes,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return MXE_OK;
+    }
+    CK(cudaMemsetAsync(c->clk, 0, sizeof(DevClock), c->stream));
+    c->slot = 0;
+    int nt = 256;
+    dim3 grid((c->g.nx + nt - 1) / nt, c->g.ny);
+    mxe_rate14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
+    CK(cudaGetLastError());
+    return MXE_OK;
+}
+
+// ---------------------------------------------------------------- state I/O
+extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int on_device) {
+    if (!c) return MXE_EINVAL;
+    if (!soa) return fail(c, MXE_EINVAL, "soa is NULL");
+    if (kind != MXE_PRIMITIVE && kind != MXE_CONSERVED)
+        return fail(c, MXE_EINVAL, "kind must be PRIMITIVE or CONSERVED");
+    size_t bytes = sizeof(double) * c->nf * c->ncell;
+    const double* src = soa;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->stage, soa, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->stage;
+    }
+    unsigned long long init = ~0ull;
+    CK(cudaMemcpyAsync(c->scratch, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    CellMap m = cellmap(c);
+    dim3 grid = cellgrid(c, 128);
+    mxe_k_validate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->scratch);
+    CK(cudaGetLastError());
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, c->scratch, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (bad != ~0ull) {
+        unsigned long long idx = bad >> 2;
+        int code = (int)(bad & 3);
+        const char* why = code == 1 ? "non-finite value"
+                        : code == 2 ? "rho <= 0 or pressure tensor not positive definite"
+                                    : "sigma > 1 (outside the realizability boundary)";
+        return fail(c, code == 1 ? MXE_ENONFINITE : MXE_EUNREALIZABLE,
+                    "input cell %llu: %s", idx, why);
+    }
+    mxe_k_setstate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->U);
+    CK(cudaGetLastError());
+    mxe_status s = reset_clock(c);
+    if (s != MXE_OK) return s;
+    c->have_state = true;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_get_moments(mxe_ctx* c, int kind, double* soa, int on_device) {
+    if (!c) return MXE_EINVAL;
+    if (!soa) return fail(c, MXE_EINVAL, "soa is NULL");
+    if (kind < 0 || kind > 2) return fail(c, MXE_EINVAL, "bad kind %d", kind);
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    int nfo = kind == MXE_SIGMA ? 1 : c->nf;
+    double* dst = on_device ? soa : c->stage;
+    CellMap m = cellmap(c);
+    mxe_k_getstate<<<cellgrid(c, 128), 128, 0, c->stream>>>(m, c->nf, kind, c->U, dst);
+    CK(cudaGetLastError());
+    if (!on_device)
+        CK(cudaMemcpyAsync(soa, c->stage, sizeof(double) * nfo * c->ncell, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MXE_OK;
+}
+
+// ---------------------------------------------------------------- BCs, tau
+static mxe_status upload_ghosts(mxe_ctx* c) {
+    CK(cudaMemcpyAsync(c->ghost_in, c->ghost_h, sizeof c->ghost_h, cudaMemcpyHostToDevice,
+                       c->stream));
+    int n = 4 * GHOST_SLOTS;
+    mxe_k_ghost<<<1, 32, 0, c->stream>>>(c->nf, n, c->ghost_in, c->ghost_d);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    // 2D side descriptors: index ranges of the slots along each side
+    if (!c->tubes) {
+        for (int s = 0; s < 4; ++s) {
+            SideDesc& sd = c->g.side[s];
+            sd.type = c->bc_type[s];
+            sd.nspans = 0;
+            int ncell_side = s < 2 ? c->g.ny : c->g.nx;
+            double o = s < 2 ? c->cfg.y0 : c->cfg.x0;
+            double h = s < 2 ? (c->cfg.y1 - c->cfg.y0) / c->cfg.ny : (c->cfg.x1 - c->cfg.x0) / c->cfg.nx;
+            for (int n2 = 0; n2 < c->nspans[s]; ++n2) {
+                int lo = -1, hi = -2;
+                for (int j = 0; j < ncell_side; ++j) {
+                    double xt = o + ((double)j + 0.5) * h;
+                    if (xt >= c->span_lo[s][n2] && xt <= c->span_hi[s][n2]) {
+                        if (lo < 0) lo = j;
+                        hi = j;
+                    }
+                }
+                sd.lo[sd.nspans] = lo < 0 ? 1 : lo;
+                sd.hi[sd.nspans] = lo < 0 ? 0 : hi;      // empty range if no cell
+                ++sd.nspans;
+            }
+        }
+        c->g.ghost = c->ghost_d;
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_bc(mxe_ctx* c, int side, int type, double lo, double hi,
+                                 const double* prim) {
+    if (!c) return MXE_EINVAL;
+    int nsides = c->tubes ? 2 : 4;
+    if (side < 0 || side >= nsides) return fail(c, MXE_EINVAL, "bad side %d", side);
+    if (type < 0 || type > 2) return fail(c, MXE_EINVAL, "bad BC type %d", type);
+    if (type == MXE_BC_DIRICHLET && !prim) return fail(c, MXE_EINVAL, "Dirichlet needs a state");
+    if (type == MXE_BC_DIRICHLET) {
+        // the imposed state must itself be admissible
+        for (int k = 0; k < c->nf; ++k)
+            if (!std::isfinite(prim[k])) return fail(c, MXE_EINVAL, "non-finite BC state");
+        if (!(prim[0] > 0.0)) return fail(c, MXE_EUNREALIZABLE, "BC state with rho <= 0");
+    }
+    if (type == MXE_BC_DIRICHLET && lo < hi) {
+        if (c->tubes) return fail(c, MXE_EINVAL, "inflow slots need a 2D grid");
+        if (c->nspans[side] >= MAX_SPANS) return fail(c, MXE_EINVAL, "at most %d slots", MAX_SPANS);
+        int n = c->nspans[side]++;
+        c->span_lo[side][n] = lo;
+        c->span_hi[side][n] = hi;
+        for (int k = 0; k < 14; ++k) c->ghost_h[side][1 + n][k] = k < c->nf ? prim[k] : 0.0;
+    } else {
+        c->bc_type[side] = type;
+        c->nspans[side] = 0;
+        if (type == MXE_BC_DIRICHLET)
+            for (int k = 0; k < 14; ++k) c->ghost_h[side][0][k] = k < c->nf ? prim[k] : 0.0;
+    }
+    return upload_ghosts(c);
+}
+
+extern "C" mxe_status mxe_set_relaxation(mxe_ctx* c, int model, double tau_ref, double rho_ref,
+                                         double T_ref) {
+    if (!c) return MXE_EINVAL;
+    if (model < 0 || model > 2) return fail(c, MXE_EINVAL, "bad relaxation model %d", model);
+    if (model != 0 && !(tau_ref > 0.0)) return fail(c, MXE_EINVAL, "tau_ref must be > 0");
+    if (model == 2 && !(rho_ref > 0.0 && T_ref > 0.0))
+        return fail(c, MXE_EINVAL, "rho_ref and T_ref must be > 0");
+    c->rp = RelaxParams{model, tau_ref, rho_ref, T_ref};
+    if (c->tubes) {
+        for (auto& td : c->tdesc) td.rp = c->rp;
+        CK(cudaMemcpyAsync(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * c->ntubes,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_set_relaxation(mxe_ctx* c, int tube, int model, double tau_ref,
+                                               double rho_ref, double T_ref) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes) return fail(c, MXE_ESTATE, "not a batch context");
+    if (tube < 0 || tube >= c->ntubes) return fail(c, MXE_EINVAL, "bad tube %d", tube);
+    if (model < 0 || model > 2) return fail(c, MXE_EINVAL, "bad relaxation model %d", model);
+    if (model != 0 && !(tau_ref > 0.0)) return fail(c, MXE_EINVAL, "tau_ref must be > 0");
+    c->tdesc[tube].rp = RelaxParams{model, tau_ref, rho_ref, T_ref};
+    CK(cudaMemcpyAsync(c->tdesc_d + tube, &c->tdesc[tube], sizeof(TubeDesc),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MXE_OK;
+}
+
+// ---------------------------------------------------------------- stepping
+static mxe_status periodic_ok(mxe_ctx* c) {
+    int ns = c->tubes ? 2 : 4;
+    for (int s = 0; s < ns; s += 2)
+        if ((c->bc_type[s] == MXE_BC_PERIODIC) != (c->bc_type[s + 1] == MXE_BC_PERIODIC))
+            return fail(c, MXE_EINVAL, "periodic BCs must be set on both opposite sides");
+    return MXE_OK;
+}
+
+static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed) {
+    Stage2DArgs a{};
+    a.g = c->g;
+    for (int s = 0; s < 4; ++s) a.g.side[s].type = c->bc_type[s];
+    a.sp = c->sp;
+    a.rp = c->rp;
+    a.cfl = c->cfg.cfl;
+    a.t_end = t_end;
+    a.dt_fixed = dt_fixed;
+    a.slot = c->slot;
+    a.clk = c->clk;
+    dim3 grid((c->g.nx + tile_x() - 1) / tile_x(), (c->g.ny + tile_y() - 1) / tile_y());
+    size_t smem = stage14_2d_f64_smem();
+    if (c->cfg.integrator == MXE_RK2) {
+        a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 0.5; a.final_stage = 0;
+        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+        a.Uin = c->Us; a.Ubase = c->U; a.Uout = c->U; a.coef = 1.0; a.final_stage = 1;
+        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+    } else {
+        a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 1.0; a.final_stage = 1;
+        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+        std::swap(c->U, c->Us);
+    }
+    CK(cudaGetLastError());
+    c->slot = (c->slot + 1) % 3;
+    return MXE_OK;
+}
+
+static mxe_status read_clock_2d(mxe_ctx* c, DevClock* h) {
+    CK(cudaMemcpyAsync(h, c->clk, sizeof(DevClock), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MXE_OK;
+}
+
+static mxe_status run_tubes(mxe_ctx* c, int max_steps, double t_end, const double* dts,
+                            int ndts) {
+    TubeArgs a{};
+    a.U = c->U;
+    a.Us = c->Us;
+    a.tubes = c->tdesc_d;
+    a.clk = c->tclk;
+    a.bc_type[0] = c->bc_type[0];
+    a.bc_type[1] = c->bc_type[1];
+    a.ghost = c->ghost_d;
+    a.ntubes = c->ntubes;
+    a.system = c->nf;
+    a.integrator = c->cfg.integrator;
+    a.sp = c->sp;
+    a.cfl = c->cfg.cfl;
+    a.t_end = t_end;
+    a.max_steps = max_steps;
+    if (dts) {
+        if (ndts > c->dts_cap) {
+            cudaFree(c->dts_d);
+            c->dts_d = nullptr;
+            CK(cudaMalloc(&c->dts_d, sizeof(double) * ndts));
+            c->dts_cap = ndts;
+        }
+        CK(cudaMemcpyAsync(c->dts_d, dts, sizeof(double) * ndts, cudaMemcpyHostToDevice,
+                           c->stream));
+        a.dt_fixed = c->dts_d;
+        a.n_fixed = ndts;
+        a.max_steps = ndts;
+    }
+    if (c->nf == 5) mxe_tubes5_f64<<<c->ntubes, tubes_threads(), 0, c->stream>>>(a);
+    else mxe_tubes14_f64<<<c->ntubes, tubes_threads(), 0, c->stream>>>(a);
+    CK(cudaGetLastError());
+    return MXE_OK;
+}
+
+static mxe_status tube_status(mxe_ctx* c, double* t0, long long* steps0) {
+    std::vector<TubeClock> h(c->ntubes);
+    CK(cudaMemcpyAsync(h.data(), c->tclk, sizeof(TubeClock) * c->ntubes, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t0) *t0 = h[0].t;
+    if (steps0) *steps0 = h[0].steps;
+    for (int b = 0; b < c->ntubes; ++b)
+        if (h[b].status & ST_NONFINITE)
+            return fail(c, MXE_ENONFINITE, "tube %d: non-finite state at t = %g", b, h[b].t);
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_step(mxe_ctx* c, int max_steps, double t_end, double* t_out,
+                               int* steps_out) {
+    if (!c) return MXE_EINVAL;
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    if (max_steps < 0) return fail(c, MXE_EINVAL, "max_steps < 0");
+    mxe_status s = periodic_ok(c);
+    if (s != MXE_OK) return s;
+    if (c->tubes) {
+        long long st0 = 0, st1 = 0;
+        if (steps_out) {
+            s = tube_status(c, nullptr, &st0);
+            if (s != MXE_OK) return s;
+        }
+        s = run_tubes(c, max_steps, t_end, nullptr, 0);
+        if (s != MXE_OK) return s;
+        if (t_out || steps_out) {
+            double t;
+            s = tube_status(c, &t, &st1);
+            if (t_out) *t_out = t;
+            if (steps_out) *steps_out = (int)(st1 - st0);
+            return s;
+        }
+        return MXE_OK;
+    }
+    DevClock h{};
+    long long st0 = 0;
+    bool want = t_out || steps_out;
+    if (want) {
+        s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        st0 = h.steps;
+    }
+    // launch in chunks; a step past t_end is a no-op on the device
+    int done = 0, chunk = 4;
+    while (done < max_steps) {
+        int n = std::min(chunk, max_steps - done);
+        for (int i = 0; i < n; ++i) {
+            s = launch_2d_step(c, t_end, 0.0);
+            if (s != MXE_OK) return s;
+        }
+        done += n;
+        if (done >= max_steps) break;
+        s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        if (h.status & ST_NONFINITE) break;
+        if (!(h.t[c->slot] < t_end)) break;
+        chunk = std::min(chunk * 2, 256);
+    }
+    if (want) {
+        s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        if (t_out) *t_out = h.t[c->slot];
+        if (steps_out) *steps_out = (int)(h.steps - st0);
+        if (h.status & ST_NONFINITE) return fail(c, MXE_ENONFINITE, "non-finite state");
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_step_dt(mxe_ctx* c, int n, const double* dts) {
+    if (!c) return MXE_EINVAL;
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    if (n < 0 || (n > 0 && !dts)) return fail(c, MXE_EINVAL, "bad dt list");
+    for (int i = 0; i < n; ++i)
+        if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return fail(c, MXE_EINVAL, "dt[%d] <= 0", i);
+    mxe_status s = periodic_ok(c);
+    if (s != MXE_OK) return s;
+    if (n == 0) return MXE_OK;
+    if (c->tubes) {
+        s = run_tubes(c, n, INFINITY, dts, n);
+        if (s != MXE_OK) return s;
+        return tube_status(c, nullptr, nullptr);
+    }
+    for (int i = 0; i < n; ++i) {
+        s = launch_2d_step(c, INFINITY, dts[i]);
+        if (s != MXE_OK) return s;
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_run(mxe_ctx* c, int max_steps, double t_end) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes) return fail(c, MXE_ESTATE, "not a batch context");
+    return mxe_step(c, max_steps, t_end, nullptr, nullptr);
+}
+
+extern "C" mxe_status mxe_batch_get_clock(mxe_ctx* c, double* t, long long* steps) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes) return fail(c, MXE_ESTATE, "not a batch context");
+    std::vector<TubeClock> h(c->ntubes);
+    CK(cudaMemcpyAsync(h.data(), c->tclk, sizeof(TubeClock) * c->ntubes, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->ntubes; ++b) {
+        if (t) t[b] = h[b].t;
+        if (steps) steps[b] = h[b].steps;
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_get_diagnostics(mxe_ctx* c, mxe_diag* out) {
+    if (!c || !out) return MXE_EINVAL;
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    memset(out, 0, sizeof *out);
+    double acc[32];
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    acc[16] = INFINITY;
+    unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(c->accd, acc, sizeof acc, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->scratch, cnt, sizeof cnt, cudaMemcpyHostToDevice, c->stream));
+    mxe_k_diag<<<cellgrid(c, 128), 128, 0, c->stream>>>(cellmap(c), c->nf, c->U,
+                                                        c->cfg.sigma_lim, c->accd, c->scratch);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(acc, c->accd, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(cnt, c->scratch, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < c->nf; ++k) out->sums[k] = acc[k];
+    out->min_sigma = acc[16];
+    out->n_sigma_below_lim = (long long)cnt[0];
+    out->n_sigma_above_one = (long long)cnt[1];
+    out->n_nonpositive = (long long)cnt[2];
+    out->n_nonfinite = (long long)cnt[3];
+    if (c->tubes) {
+        std::vector<TubeClock> h(c->ntubes);
+        CK(cudaMemcpy(h.data(), c->tclk, sizeof(TubeClock) * c->ntubes, cudaMemcpyDeviceToHost));
+        out->t = h[0].t;
+        out->last_dt = h[0].last_dt;
+        out->steps = h[0].steps;
+        out->max_rate = h[0].rate;
+    } else {
+        DevClock h{};
+        mxe_status s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        out->t = h.t[c->slot];
+        out->last_dt = h.last_dt;
+        out->steps = h.steps;
+        memcpy(&out->max_rate, &h.rate[c->slot], sizeof(double));
+        out->n_fp64_closures = (long long)h.n_face64;
+        out->n_closures = (long long)h.n_face;
+    }
+    return MXE_OK;
+}

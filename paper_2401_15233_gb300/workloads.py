@@ -180,3 +180,70 @@ def smooth_field14(rng, nx: int, ny: int, amp: float = 0.3, planar: bool = True)
     Z = np.zeros_like(X)
     st = np.stack([rho, ux, uy, Z, Pxx, Pxy, Z, Pyy, Z, Pzz, qx, qy, Z, R], axis=-1)
     return st
+
+
+def maxwellian_mixture14(comps):
+    """Central moments of a sum of Maxwellians [(rho_a, (ux, uy, uz), T_a), ...]
+    (Gaussian moment identities): P = sum rho_a (T_a I + c c^T),
+    q = sum rho_a c (|c|^2 + 5 T_a), R = sum rho_a (|c|^4 + 10 T_a |c|^2 + 15 T_a^2),
+    with c = u_a - u the offset of each component from the mixture velocity."""
+    rho = sum(c[0] for c in comps)
+    u = sum(c[0] * np.asarray(c[1], dtype=float) for c in comps) / rho
+    P = np.zeros((3, 3)); q = np.zeros(3); R = 0.0
+    for ra, ua, Ta in comps:
+        c = np.asarray(ua, dtype=float) - u
+        c2 = c @ c
+        P += ra * (Ta * np.eye(3) + np.outer(c, c))
+        q += ra * c * (c2 + 5 * Ta)
+        R += ra * (c2 * c2 + 10 * Ta * c2 + 15 * Ta * Ta)
+    return np.array([rho, *u, P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2], *q, R])
+
+
+def jets_like_field(nx: int, ny: int, setup: dict, spread=0.35, reach=0.8, rng=None):
+    """A synthetic, developed-looking crossed-jets state on [0,1]^2: background
+    gas plus two Maxwellian beams (the inflow states) whose densities decay
+    away from the slots and spread with distance, so that the crossing
+    region holds bimodal (strongly non-equilibrium) states.  Vectorised over
+    cells: returns (ny, nx, 14) primitives."""
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    lo, hi = setup["slot"]
+    yc, hw = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    jitter = 0.0 if rng is None else rng.uniform(-0.02, 0.02)
+
+    def beam(s, n):        # s: distance along the jet, n: transverse offset
+        w = hw + spread * s
+        prof = 0.5 * (1 - np.tanh((np.abs(n) - w) / (0.01 + 0.05 * s)))
+        return prof * (hw / w) * 0.5 * (1 - np.tanh((s - reach - jitter) / 0.05))
+
+    rb = setup["background"][0]
+    Tb = setup["background"][4] / rb
+    rj = setup["left"][0]
+    Tj = setup["left"][4] / rj
+    ux = setup["left"][1]
+    uy = setup["bottom"][2]
+    w1 = rj * beam(X, Y - yc)
+    w2 = rj * beam(Y, X - yc)
+    # vectorised mixture of three Maxwellians
+    comps = [(np.full_like(X, rb), (0.0, 0.0), Tb), (w1 + 1e-30, (ux, 0.0), Tj),
+             (w2 + 1e-30, (0.0, uy), Tj)]
+    rho = sum(c[0] for c in comps)
+    u = [sum(c[0] * c[1][d] for c in comps) / rho for d in range(2)]
+    out = np.zeros((ny, nx, 14))
+    out[..., 0] = rho
+    out[..., 1], out[..., 2] = u
+    Pxx = Pxy = Pyy = Pzz = q0 = q1 = R = 0.0
+    for ra, ua, Ta in comps:
+        cx, cy = ua[0] - u[0], ua[1] - u[1]
+        c2 = cx * cx + cy * cy
+        Pxx = Pxx + ra * (Ta + cx * cx)
+        Pyy = Pyy + ra * (Ta + cy * cy)
+        Pzz = Pzz + ra * Ta
+        Pxy = Pxy + ra * cx * cy
+        q0 = q0 + ra * cx * (c2 + 5 * Ta)
+        q1 = q1 + ra * cy * (c2 + 5 * Ta)
+        R = R + ra * (c2 * c2 + 10 * Ta * c2 + 15 * Ta * Ta)
+    out[..., 4], out[..., 5], out[..., 7], out[..., 9] = Pxx, Pxy, Pyy, Pzz
+    out[..., 10], out[..., 11], out[..., 13] = q0, q1, R
+    return out

@@ -1,0 +1,285 @@
+"""GPU parity of the FP64 CUDA path against the FP64 oracle, through the
+C-ABI.  Bar: normwise relative error per field <= 1e-12 after one stage /
+one step from identical input; multi-step trajectories are checked with the
+drift bound stated in each test."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2401_15233_gb300 import workloads as wl
+from tests._util import (aos_to_soa, cons_field, field_rel_err, jets_gpu_solver, jets_oracle_cfg,
+                         soa_to_aos)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def mx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_15233_gb300 as m
+    m.lib()
+    return m
+
+
+def gpu_cons(s):
+    return soa_to_aos(s.get_moments("conserved"))
+
+
+# ------------------------------------------------------------------ 1D, 5-moment (config 1)
+def sod5_pair(mx, orc, nx, Kn, order=1, integ="fe", flux="hll"):
+    prim = wl.sod_prim(5, nx)
+    s = mx.Solver(system=5, nx=nx, ny=1, order=order, integrator=integ, flux=flux)
+    s.set_state(aos_to_soa(prim[None]))
+    s.set_relaxation(mx.TAU_HARDSPHERE, wl.sod_tau_ref(Kn), 1.0, 1.0)
+    cfg = orc.make_cfg(system=5, nx=nx, ny=1, order=order,
+                       integrator=0 if integ == "fe" else 1, flux=0 if flux == "hll" else 1,
+                       tau_model=2, tau_ref=wl.sod_tau_ref(Kn))
+    return s, cfg, cons_field(orc, prim[None])
+
+
+def test_sod5_single_step_and_dt(mx, orc):
+    s, cfg, U = sod5_pair(mx, orc, 1000, 0.01)
+    dt_o = orc.dt(cfg, U, 0.0, 0.2)
+    t, n = s.step(1, 0.2)
+    assert n == 1
+    assert t == pytest.approx(dt_o, rel=TOL)
+    U1 = orc.step(cfg, U, dt_o)
+    assert field_rel_err(gpu_cons(s), U1).max() <= TOL
+
+
+def test_sod5_config1_to_t02(mx, orc):
+    """Config 1 to t = 0.2 (about 1.4e4 forward-Euler steps)."""
+    s, cfg, U = sod5_pair(mx, orc, 1000, 0.01)
+    t, n = s.step(10 ** 6, 0.2)
+    Uo, to, hist = orc.run(cfg, U, 0.0, 0.2, 10 ** 6)
+    assert t == pytest.approx(0.2, rel=1e-14) and to == pytest.approx(0.2, rel=1e-14)
+    assert n == len(hist)
+    err = field_rel_err(gpu_cons(s), Uo)
+    print("config-1 trajectory drift per field:", err)
+    assert err.max() <= 1e-9
+    d = s.diagnostics()
+    assert d["n_sigma_above_one"] == 0 and d["n_nonfinite"] == 0
+
+
+# ------------------------------------------------------------------ 1D, 14-moment (config 2)
+@pytest.mark.parametrize("Kn", [1e-3, 1e-2, 0.1, 1.0, 10.0])
+def test_sod14_1d_parity(mx, orc, Kn):
+    nx = 256
+    prim = wl.sod_prim(14, nx)
+    s = mx.Solver(system=14, nx=nx, ny=1)
+    s.set_state(aos_to_soa(prim[None]))
+    s.set_relaxation(mx.TAU_HARDSPHERE, wl.sod_tau_ref(Kn), 1.0, 1.0)
+    cfg = orc.make_cfg(system=14, nx=nx, ny=1, tau_model=2, tau_ref=wl.sod_tau_ref(Kn))
+    U = cons_field(orc, prim[None])
+    dt_o = orc.dt(cfg, U, 0.0, 0.2)
+    t, n = s.step(1, 0.2)
+    assert t == pytest.approx(dt_o, rel=TOL)
+    U = orc.step(cfg, U, dt_o)
+    assert field_rel_err(gpu_cons(s), U).max() <= TOL
+    # 150 more steps on each side's own CFL clock
+    t_g, n_g = s.step(150, 0.2)
+    Uo, to, hist = orc.run(cfg, U, dt_o, 0.2, 150)
+    assert t_g == pytest.approx(to, rel=1e-12)
+    err = field_rel_err(gpu_cons(s), Uo)
+    print(f"Kn={Kn}: 151-step drift", err.max())
+    assert err.max() <= 1e-10
+
+
+# ------------------------------------------------------------------ 2D, 14-moment
+@pytest.mark.parametrize("nx,ny", [(40, 37), (15, 16), (4, 4), (31, 17)])
+def test_jets2d_one_step(mx, orc, nx, ny):
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(nx * 100 + ny)
+    prim = wl.jets_like_field(nx, ny, setup, rng=rng)
+    s = jets_gpu_solver(mx, nx, ny, setup)
+    s.set_state(aos_to_soa(prim))
+    cfg = jets_oracle_cfg(orc, nx, ny, setup)
+    U = cons_field(orc, prim)
+    dt_o = orc.dt(cfg, U, 0.0, 10.0)
+    t, n = s.step(1, 10.0)
+    assert t == pytest.approx(dt_o, rel=TOL)
+    err = field_rel_err(gpu_cons(s), orc.step(cfg, U, dt_o))
+    assert err.max() <= TOL, err
+
+
+def test_jets2d_trajectory_from_rest(mx, orc):
+    """Config 3 geometry from the uniform background, 24 steps at 48^2."""
+    n = 48
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_initial(n, n, setup)
+    s = jets_gpu_solver(mx, n, n, setup)
+    s.set_state(aos_to_soa(prim))
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    U = cons_field(orc, prim)
+    t_g, n_g = s.step(24, 10.0)
+    Uo, to, hist = orc.run(cfg, U, 0.0, 10.0, 24)
+    assert n_g == 24 and t_g == pytest.approx(to, rel=1e-12)
+    err = field_rel_err(gpu_cons(s), Uo)
+    print("jets 24-step drift", err.max())
+    assert err.max() <= 1e-10
+
+
+@pytest.mark.parametrize("variant", ["fe_order1", "rusanov", "vanalbada", "k12"])
+def test_jets2d_scheme_variants(mx, orc, variant):
+    nx, ny = 33, 30
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(nx, ny, setup)
+    kw, okw = {}, {}
+    if variant == "fe_order1":
+        kw = dict(order=1, integrator="fe"); okw = dict(order=1, integ=0)
+    elif variant == "rusanov":
+        kw = dict(flux="rusanov"); okw = dict(flux=1)
+    elif variant == "vanalbada":
+        kw = dict(limiter="vanalbada"); okw = dict(limiter=1)
+    s = jets_gpu_solver(mx, nx, ny, setup, **kw)
+    cfg = jets_oracle_cfg(orc, nx, ny, setup, **okw)
+    if variant == "k12":
+        s.close()
+        s = mx.Solver(system=14, nx=nx, ny=ny, k_ws=1.2)
+        lo, hi = setup["slot"]
+        s.set_bc(mx.XLO, mx.BC_DIRICHLET, lo, hi, setup["left"])
+        s.set_bc(mx.YLO, mx.BC_DIRICHLET, lo, hi, setup["bottom"])
+        s.set_relaxation(mx.TAU_HARDSPHERE, setup["tau_ref"], setup["rho_ref"], setup["T_ref"])
+        cfg.k_ws = 1.2
+    s.set_state(aos_to_soa(prim))
+    U = cons_field(orc, prim)
+    for _ in range(3):
+        dt_o = orc.dt(cfg, U, 0.0, 10.0)
+        s.step_dt([dt_o])
+        U = orc.step(cfg, U, dt_o)
+        err = field_rel_err(gpu_cons(s), U)
+        assert err.max() <= 1e-11, (variant, err)
+
+
+def test_periodic_2d_parity_and_conservation(mx, orc):
+    nx, ny = 34, 21
+    rng = np.random.default_rng(7)
+    prim = wl.smooth_field14(rng, nx, ny, amp=0.4)
+    s = mx.Solver(system=14, nx=nx, ny=ny)
+    for side in range(4):
+        s.set_bc(side, mx.BC_PERIODIC)
+    s.set_relaxation(mx.TAU_CONST, 0.05)
+    s.set_state(aos_to_soa(prim))
+    cfg = orc.make_cfg(system=14, nx=nx, ny=ny, tau_model=1, tau_ref=0.05,
+                       sides=[{"type": 1}] * 4)
+    U = cons_field(orc, prim)
+    d0 = s.diagnostics()
+    t_g, n_g = s.step(40, 10.0)
+    Uo, to, hist = orc.run(cfg, U, 0.0, 10.0, 40)
+    err = field_rel_err(gpu_cons(s), Uo)
+    assert err.max() <= 1e-10, err
+    d1 = s.diagnostics()
+    for k in (0, 1, 2, 3):
+        assert abs(d1["sums"][k] - d0["sums"][k]) <= 1e-12 * abs(d0["sums"][0])
+    e0 = d0["sums"][4] + d0["sums"][7] + d0["sums"][9]
+    e1 = d1["sums"][4] + d1["sums"][7] + d1["sums"][9]
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+
+
+def test_uniform_state_bitwise_2d(mx):
+    rng = np.random.default_rng(3)
+    Q = wl.random_prim14(rng, 1, planar=True)[0]
+    nx, ny = 23, 19
+    prim = np.broadcast_to(Q, (ny, nx, 14)).copy()
+    s = mx.Solver(system=14, nx=nx, ny=ny)
+    for side in range(4):
+        s.set_bc(side, mx.BC_PERIODIC)
+    s.set_state(aos_to_soa(prim))
+    U0 = s.get_moments("conserved")
+    s.step(5, 10.0)
+    assert np.array_equal(s.get_moments("conserved"), U0)
+
+
+# ------------------------------------------------------------------ batched tubes
+def test_batch_tubes_parity(mx, orc):
+    tubes = wl.batch_tubes(6, nmin=40, nmax=300)
+    ncells = [t[0] for t in tubes]
+    b = mx.Batch(ncells, [1.0] * len(tubes), system=14)
+    prims = []
+    for (nc, kn, ratio) in tubes:
+        prims.append(aos_to_soa(wl.sod_prim(14, nc, rhoR=1 / ratio, PR=1 / ratio)[None])[:, 0])
+    b.set_state(b.pack(prims))
+    for i, (nc, kn, ratio) in enumerate(tubes):
+        b.set_tube_relaxation(i, mx.TAU_HARDSPHERE, wl.sod_tau_ref(kn), 1.0, 1.0)
+    b.run(40, 0.2)
+    t_g, st_g = b.clock()
+    out = b.unpack(b.get_moments("conserved"))
+    for i, (nc, kn, ratio) in enumerate(tubes):
+        cfg = orc.make_cfg(system=14, nx=nc, ny=1, tau_model=2, tau_ref=wl.sod_tau_ref(kn))
+        U = cons_field(orc, wl.sod_prim(14, nc, rhoR=1 / ratio, PR=1 / ratio)[None])
+        Uo, to, hist = orc.run(cfg, U, 0.0, 0.2, 40)
+        assert st_g[i] == len(hist)
+        assert t_g[i] == pytest.approx(to, rel=1e-12)
+        err = field_rel_err(soa_to_aos(out[i][:, None, :]), Uo)
+        assert err.max() <= 1e-10, (i, err)
+
+
+# ------------------------------------------------------------------ full size, sampled
+def sampled_window_check(mx, orc, n, windows, dt):
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(n, n, setup)
+    s = jets_gpu_solver(mx, n, n, setup)
+    s.set_state(aos_to_soa(prim))
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    s.step_dt([dt])
+    G = s.get_moments("conserved")
+    worst = 0.0
+    for (i0, j0, w, h) in windows:
+        M = 4
+        ii = np.clip(np.arange(i0 - M, i0 + w + M), 0, n - 1)
+        jj = np.clip(np.arange(j0 - M, j0 + h + M), 0, n - 1)
+        Ub = cons_field(orc, prim[np.ix_(jj, ii)])
+        ref = orc.block_step(cfg, i0, j0, w, h, Ub, dt)
+        got = soa_to_aos(G[:, j0:j0 + h, i0:i0 + w])
+        e = field_rel_err(got, ref).max()
+        worst = max(worst, e)
+        assert e <= TOL, ((i0, j0), e)
+    return worst
+
+
+def test_sampled_parity_1024(mx, orc):
+    n = 1024
+    wins = [(0, 0, 16, 16), (0, 456, 16, 24), (456, 0, 24, 16), (500, 500, 20, 20),
+            (1008, 1008, 16, 16), (1008, 300, 16, 16), (700, 515, 17, 13), (3, 1010, 9, 14)]
+    sampled_window_check(mx, orc, n, wins, 2e-5)
+
+
+def test_sampled_parity_4096_bench_config(mx, orc):
+    n = 4096
+    wins = [(0, 1843, 16, 24), (1843, 0, 24, 16), (2040, 2040, 16, 16), (4080, 4080, 16, 16),
+            (2900, 2050, 15, 16)]
+    sampled_window_check(mx, orc, n, wins, 5e-6)
+
+
+# ------------------------------------------------------------------ errors and edge cases
+def test_input_validation_errors(mx):
+    s = mx.Solver(system=14, nx=8, ny=8)
+    with pytest.raises(mx.MaxentError) as e:
+        s.step(1, 1.0)
+    assert e.value.status == mx.ESTATE
+    good = np.broadcast_to(wl.maxwellian14(1.0, 0, 0, 1.0), (8, 8, 14)).copy()
+    bad = good.copy(); bad[3, 4, 0] = -1.0
+    with pytest.raises(mx.MaxentError) as e:
+        s.set_state(aos_to_soa(bad))
+    assert e.value.status == mx.EUNREALIZABLE and "cell 28" in str(e.value)
+    bad = good.copy(); bad[0, 1, 13] = np.nan
+    with pytest.raises(mx.MaxentError) as e:
+        s.set_state(aos_to_soa(bad))
+    assert e.value.status == mx.ENONFINITE
+    bad = good.copy(); bad[2, 2, 13] = 0.5 * bad[2, 2, 13]    # kurtosis below the boundary
+    with pytest.raises(mx.MaxentError) as e:
+        s.set_state(aos_to_soa(bad))
+    assert e.value.status == mx.EUNREALIZABLE
+    s.set_state(aos_to_soa(good))
+    s.set_bc(mx.XLO, mx.BC_PERIODIC)
+    with pytest.raises(mx.MaxentError) as e:
+        s.step(1, 1.0)
+    assert e.value.status == mx.EINVAL
+    s.set_bc(mx.XHI, mx.BC_PERIODIC)
+    s.step(2, 1.0)
+    with pytest.raises(mx.MaxentError):
+        s.set_bc(7, mx.BC_TRANSMISSIVE)
