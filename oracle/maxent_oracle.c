@@ -626,6 +626,8 @@ typedef struct {
     int mx, my;           /* margins                        */
     int W, H;             /* stored extent (w+2mx, h+2my)   */
     int nf;
+    double *gp;           /* per-cell imposed primitive state of Dirichlet
+                             ghosts (gp[cell*nf] is NaN where none)        */
 } blk;
 
 static double *cell(const blk *b, double *A, int i, int j) {
@@ -642,21 +644,27 @@ static int side_is_boundary(const or_cfg *c, const blk *b, int s) {
 }
 
 /* Ghost value for a cell of side s whose tangential centre coordinate is
- * xt, given the nearest interior cell value Uin (conserved). */
+ * xt, given the nearest interior cell value Uin (conserved).  Reading
+ * (Sec. 6, inflow values imposed in the ghost cells; Sec. 3.2,
+ * reconstruction of primitive variables): a Dirichlet ghost carries the
+ * imposed primitive state itself, Gp; its conserved value Ug is stored too. */
 static void ghost_value(const or_cfg *c, int s, double xt, const double *Uin,
-                        double *Ug) {
+                        double *Ug, double *Gp) {
     const or_side *sd = &c->side[s];
     int nf = nfields(c);
     for (int n = 0; n < sd->nspans; ++n)
         if (xt >= sd->span_lo[n] && xt <= sd->span_hi[n]) {
             prim2cons(c, sd->span_state[n], Ug);
+            memcpy(Gp, sd->span_state[n], nf * sizeof(double));
             return;
         }
     if (sd->base_type == OR_BC_DIRICHLET) {
         prim2cons(c, sd->base_state, Ug);
+        memcpy(Gp, sd->base_state, nf * sizeof(double));
         return;
     }
     for (int k = 0; k < nf; ++k) Ug[k] = Uin[k];          /* transmissive */
+    Gp[0] = NAN;
 }
 
 /* Fill two ghost layers on every side of the block that is a domain
@@ -672,7 +680,8 @@ static void fill_bc(const or_cfg *c, const blk *b, double *A) {
                 int iin = (s == 0) ? 0 : b->w - 1;
                 for (int g = 1; g <= 2; ++g) {
                     int ig = (s == 0) ? -g : b->w - 1 + g;
-                    ghost_value(c, s, yt, cell(b, A, iin, j), cell(b, A, ig, j));
+                    ghost_value(c, s, yt, cell(b, A, iin, j), cell(b, A, ig, j),
+                                cell(b, b->gp, ig, j));
                 }
             }
         } else {
@@ -681,7 +690,8 @@ static void fill_bc(const or_cfg *c, const blk *b, double *A) {
                 int jin = (s == 2) ? 0 : b->h - 1;
                 for (int g = 1; g <= 2; ++g) {
                     int jg = (s == 2) ? -g : b->h - 1 + g;
-                    ghost_value(c, s, xt, cell(b, A, i, jin), cell(b, A, i, jg));
+                    ghost_value(c, s, xt, cell(b, A, i, jin), cell(b, A, i, jg),
+                                cell(b, b->gp, i, jg));
                 }
             }
         }
@@ -697,7 +707,10 @@ static void residual_region(const or_cfg *c, const blk *b, double *A,
     double dy = (c->y1 - c->y0) / c->ny;
     size_t ncell = (size_t)b->W * b->H;
     double *Qp = (double *)malloc(ncell * nf * sizeof(double));
-    for (size_t n = 0; n < ncell; ++n) cons2prim(c, A + n * nf, Qp + n * nf);
+    for (size_t n = 0; n < ncell; ++n) {
+        if (!isnan(b->gp[n * nf])) memcpy(Qp + n * nf, b->gp + n * nf, nf * sizeof(double));
+        else cons2prim(c, A + n * nf, Qp + n * nf);
+    }
     int rw = xb - xa;
     /* L[(j-ya)*rw + (i-xa)] */
     for (int j = ya; j < yb; ++j)
@@ -759,6 +772,9 @@ static void blk_init(const or_cfg *c, blk *b, int i0, int j0, int w, int h) {
     b->W = w + 2 * b->mx;
     b->H = h + 2 * b->my;
     b->nf = nfields(c);
+    size_t n = (size_t)b->W * b->H * b->nf;
+    b->gp = (double *)malloc(n * sizeof(double));
+    for (size_t k = 0; k < n; ++k) b->gp[k] = NAN;
 }
 
 int or_block_residual(const or_cfg *c, int i0, int j0, int w, int h,
@@ -771,6 +787,7 @@ int or_block_residual(const or_cfg *c, int i0, int j0, int w, int h,
     fill_bc(c, &b, A);
     residual_region(c, &b, A, 0, w, 0, h, Lout);
     free(A);
+    free(b.gp);
     return 0;
 }
 
@@ -798,6 +815,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
             }
         free(L);
         free(A);
+        free(b.gp);
         return 0;
     }
     /* stage 1 on the interior plus 2 layers into every cut side */
@@ -834,6 +852,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
     free(S);
     free(L);
     free(A);
+    free(b.gp);
     return 0;
 }
 
@@ -894,6 +913,7 @@ int or_step(const or_cfg *c, double *U, double dt) {
             }
     int rc = or_block_step(c, 0, 0, c->nx, c->ny, A, dt, U);
     free(A);
+    free(b.gp);
     return rc;
 }
 

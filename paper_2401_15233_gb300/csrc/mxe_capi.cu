@@ -404,9 +404,10 @@ extern "C" mxe_status mxe_get_moments(mxe_ctx* c, int kind, double* soa, int on_
 static mxe_status upload_ghosts(mxe_ctx* c) {
     CK(cudaMemcpyAsync(c->ghost_in, c->ghost_h, sizeof c->ghost_h, cudaMemcpyHostToDevice,
                        c->stream));
-    int n = 4 * GHOST_SLOTS;
-    mxe_k_ghost<<<1, 32, 0, c->stream>>>(c->nf, n, c->ghost_in, c->ghost_d);
-    CK(cudaGetLastError());
+    // Dirichlet ghosts carry the imposed primitive state itself (the
+    // reconstruction acts on primitives), so no conversion is applied.
+    CK(cudaMemcpyAsync(c->ghost_d, c->ghost_in, sizeof c->ghost_h, cudaMemcpyDeviceToDevice,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
     // 2D side descriptors: index ranges of the slots along each side
     if (!c->tubes) {

@@ -92,7 +92,7 @@ __device__ __forceinline__ void load_prim_f64(const Stage2DArgs& a, int gi, int 
     double U[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) U[k] = __ldg(p + k * g.fstride);
-    cons2prim14(U, Q);
+    cons2prim14_rn(U, Q);
 }
 
 // Numerical face flux from two face states (HLL with Davis speeds, or
@@ -145,11 +145,11 @@ __device__ __forceinline__ T shared_phi_box(const T* W, int c, int stride, int l
 template <class T>
 __device__ __forceinline__ void face_state_box(const T* W, int c, int stride, T phi, T sgn,
                                                T* Qf) {
+    T hs = mul_rn(sgn, T(0.5));
 #pragma unroll
     for (int k = 0; k < 14; ++k) {
         const T* w = W + k * BX * BY + c;
-        T cen = T(0.5) * ((w[0] - w[-stride]) + (w[stride] - w[0]));
-        Qf[k] = w[0] + sgn * T(0.5) * (phi * cen);
+        Qf[k] = muscl_face(w[-stride], w[0], w[stride], phi, hs);
     }
 }
 
@@ -282,14 +282,16 @@ mxe_stage14_2d_f64(const Stage2DArgs a) {
             double Un[14];
             bool bad = false;
 #pragma unroll
+            double cdt = mul_rn(a.coef, dt);
+#pragma unroll
             for (int k = 0; k < 14; ++k) {
-                Un[k] = a.Ubase[o + k * g.fstride] + a.coef * dt * L[k];
+                Un[k] = add_rn(a.Ubase[o + k * g.fstride], mul_rn(cdt, L[k]));
                 a.Uout[o + k * g.fstride] = Un[k];
                 bad |= !isfinite(Un[k]);
             }
             if (a.final_stage) {
                 double Qn[14];
-                cons2prim14(Un, Qn);
+                cons2prim14_rn(Un, Qn);
                 if (Qn[0] <= 0.0 || Qn[4] <= 0.0 || Qn[7] <= 0.0 || Qn[9] <= 0.0)
                     atomicOr(&a.clk->status, ST_NONPOSITIVE);
                 if (bad) atomicOr(&a.clk->status, ST_NONFINITE);
@@ -322,7 +324,7 @@ extern "C" __global__ void mxe_rate14_2d(const double* U, Grid2D g, SchemeParams
         double Un[14], Qn[14];
 #pragma unroll
         for (int k = 0; k < 14; ++k) Un[k] = U[o + k * g.fstride];
-        cons2prim14(Un, Qn);
+        cons2prim14_rn(Un, Qn);
         Dimless14<double> d;
         dimless14(Qn, d);
         double ax = amax14<double, 0>(Qn, d, sp);

@@ -36,6 +36,17 @@ template <> struct M<float> {
     static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 };
 
+// Explicitly rounded operations (never fused into FMA by the compiler).
+// Used where a result feeds a branch of the scheme (primitive recovery, the
+// limiter, face reconstruction, the stage update) so that those values are
+// rounded exactly as in the reference evaluation order.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
 struct SchemeParams {
     double sigma_lim;    // Appendix A
     double k_ws;         // Sec. 5.1 inflation
@@ -92,6 +103,20 @@ __device__ __forceinline__ void cons2prim5(const T* U, T* Q) {
     T P = U[2] - rho * u * u;
     T q = U[3] - rho * u * u * u - T(3) * u * P;
     T r = U[4] - rho * u * u * u * u - T(6) * u * u * P - T(4) * u * q;
+    Q[0] = rho; Q[1] = u; Q[2] = P; Q[3] = q; Q[4] = r;
+}
+
+// Primitive recovery with every operation explicitly rounded, in the order
+// rho, u = U1/rho, P = U2 - (rho u) u, q = U3 - ((rho u) u) u - (3u) P,
+// r = U4 - (((rho u) u) u) u - ((6u) u) P - (4u) q.
+__device__ __forceinline__ void cons2prim5_rn(const double* U, double* Q) {
+    double rho = U[0];
+    double u = U[1] / rho;
+    double ru = mul_rn(rho, u), ruu = mul_rn(ru, u), ruuu = mul_rn(ruu, u);
+    double P = sub_rn(U[2], ruu);
+    double q = sub_rn(sub_rn(U[3], ruuu), mul_rn(mul_rn(3.0, u), P));
+    double r = sub_rn(sub_rn(sub_rn(U[4], mul_rn(ruuu, u)), mul_rn(mul_rn(mul_rn(6.0, u), u), P)),
+                      mul_rn(mul_rn(4.0, u), q));
     Q[0] = rho; Q[1] = u; Q[2] = P; Q[3] = q; Q[4] = r;
 }
 
@@ -222,6 +247,49 @@ __device__ __forceinline__ void cons2prim14(const T* U, T* Q) {
     Q[0] = rho; Q[1] = ux; Q[2] = uy; Q[3] = uz;
     Q[4] = Pxx; Q[5] = Pxy; Q[6] = Pxz; Q[7] = Pyy; Q[8] = Pyz; Q[9] = Pzz;
     Q[10] = qx; Q[11] = qy; Q[12] = qz; Q[13] = R;
+}
+
+// Primitive recovery with every operation explicitly rounded (sums in index
+// order, products left to right):
+//   u_i = U_i/rho, P_ij = E_ij - (rho u_i) u_j, |u|^2, tr P,
+//   u.P.u = sum_i sum_j (u_i u_j) P_ij,
+//   q_i = ((H_i - (rho u_i)|u|^2) - u_i tr P) - 2 (sum_j u_j P_ij),
+//   R = (((E4 - (rho |u|^2)|u|^2) - (2|u|^2) tr P) - 4 u.P.u) - 4 u.q
+__device__ __forceinline__ void cons2prim14_rn(const double* U, double* Q) {
+    double rho = U[0];
+    double u[3] = {U[1] / rho, U[2] / rho, U[3] / rho};
+    double P[3][3];
+    int idx = 4;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            P[i][j] = sub_rn(U[idx++], mul_rn(mul_rn(rho, u[i]), u[j]));
+            P[j][i] = P[i][j];
+        }
+    double u2 = add_rn(add_rn(mul_rn(u[0], u[0]), mul_rn(u[1], u[1])), mul_rn(u[2], u[2]));
+    double trP = add_rn(add_rn(P[0][0], P[1][1]), P[2][2]);
+    double uPu = mul_rn(mul_rn(u[0], u[0]), P[0][0]);
+#pragma unroll
+    for (int n = 1; n < 9; ++n) {
+        int i = n / 3, j = n % 3;
+        uPu = add_rn(uPu, mul_rn(mul_rn(u[i], u[j]), P[i][j]));
+    }
+    double q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double uP = add_rn(add_rn(mul_rn(u[0], P[i][0]), mul_rn(u[1], P[i][1])), mul_rn(u[2], P[i][2]));
+        q[i] = sub_rn(sub_rn(sub_rn(U[10 + i], mul_rn(mul_rn(rho, u[i]), u2)), mul_rn(u[i], trP)),
+                      mul_rn(2.0, uP));
+    }
+    double uq = add_rn(add_rn(mul_rn(u[0], q[0]), mul_rn(u[1], q[1])), mul_rn(u[2], q[2]));
+    double R = sub_rn(sub_rn(sub_rn(sub_rn(U[13], mul_rn(mul_rn(rho, u2), u2)),
+                                    mul_rn(mul_rn(2.0, u2), trP)),
+                             mul_rn(4.0, uPu)),
+                      mul_rn(4.0, uq));
+    Q[0] = rho; Q[1] = u[0]; Q[2] = u[1]; Q[3] = u[2];
+    Q[4] = P[0][0]; Q[5] = P[0][1]; Q[6] = P[0][2]; Q[7] = P[1][1]; Q[8] = P[1][2]; Q[9] = P[2][2];
+    Q[10] = q[0]; Q[11] = q[1]; Q[12] = q[2]; Q[13] = R;
 }
 
 // symmetric products
@@ -477,13 +545,22 @@ __device__ __forceinline__ T tau_of(const RelaxParams& rp, const T* Q, int syste
 // (minmod) or 2 dm dp/(dm^2 + dp^2) (van Albada).
 template <class T>
 __device__ __forceinline__ T phi_field(T dm, T dp, int lim) {
-    if (dm * dp > T(0)) {
-        if (lim == 1) return T(2) * dm * dp / (dm * dm + dp * dp);
+    if (mul_rn(dm, dp) > T(0)) {
+        if (lim == 1)
+            return mul_rn(mul_rn(T(2), dm), dp) / add_rn(mul_rn(dm, dm), mul_rn(dp, dp));
         T am = fabs(dm), ap = fabs(dp);
         T mn = am < ap ? am : ap;
-        return mn / (T(0.5) * (am + ap));
+        return mn / mul_rn(T(0.5), add_rn(am, ap));
     }
     return (dm == T(0) && dp == T(0)) ? T(1) : T(0);
+}
+
+// MUSCL face value Q0 + sgn/2 (phi c) with the central difference
+// c = ((Q0 - Qm) + (Qp - Q0))/2, explicitly rounded.
+template <class T>
+__device__ __forceinline__ T muscl_face(T qm, T q0, T qp, T phi, T half_sgn) {
+    T cen = mul_rn(T(0.5), add_rn(sub_rn(q0, qm), sub_rn(qp, q0)));
+    return add_rn(q0, mul_rn(half_sgn, mul_rn(phi, cen)));
 }
 
 }  // namespace mxe

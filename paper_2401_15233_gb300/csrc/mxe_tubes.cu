@@ -20,7 +20,7 @@ constexpr int BOX1 = C1 + 4;          // staged cells per chunk
 
 template <int NF> struct Sys;
 template <> struct Sys<5> {
-    static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim5(U, Q); }
+    static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim5_rn(U, Q); }
     static __device__ __forceinline__ void prim2cons(const double* Q, double* U) { prim2cons5(Q, U); }
     static __device__ __forceinline__ void eval(const double* Q, const SchemeParams& sp, double* U,
                                                 double* F, double& lo, double& hi) {
@@ -36,7 +36,7 @@ template <> struct Sys<5> {
     }
 };
 template <> struct Sys<14> {
-    static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim14(U, Q); }
+    static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim14_rn(U, Q); }
     static __device__ __forceinline__ void prim2cons(const double* Q, double* U) { prim2cons14(Q, U); }
     static __device__ __forceinline__ void eval(const double* Q, const SchemeParams& sp, double* U,
                                                 double* F, double& lo, double& hi) {
@@ -159,10 +159,8 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 const double* w = W + k * BOX1;
-                double cenl = 0.5 * ((w[cl] - w[cl - 1]) + (w[cl + 1] - w[cl]));
-                double cenr = 0.5 * ((w[cr] - w[cr - 1]) + (w[cr + 1] - w[cr]));
-                QL[k] = w[cl] + 0.5 * (pl * cenl);
-                QR[k] = w[cr] + -0.5 * (pr * cenr);
+                QL[k] = muscl_face(w[cl - 1], w[cl], w[cl + 1], pl, 0.5);
+                QR[k] = muscl_face(w[cr - 1], w[cr], w[cr + 1], pr, -0.5);
             }
             riemann_1d<NF>(QL, QR, a.sp, F);
 #pragma unroll
@@ -183,10 +181,11 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
             }
             double Un[NF];
             bool bad = false;
+            double cdt = mul_rn(coef, dt);
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 L[k] -= (Fb[k * NT1 + tid + 1] - Fb[k * NT1 + tid]) / td.dx;
-                Un[k] = base[(long long)k * n + i] + coef * dt * L[k];
+                Un[k] = add_rn(base[(long long)k * n + i], mul_rn(cdt, L[k]));
                 out[(long long)k * n + i] = Un[k];
                 bad |= !isfinite(Un[k]);
             }
