@@ -31,9 +31,14 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s 14-mom 2D RK2 (% HBM roofline), mixed vs FP64; adjoint/fwd ratio"
 UNIT = "cell-updates/s"
 # algorithmic bytes per cell-update (each stage reads its inputs once and
-# writes its output once): FP64 stage 1 reads U^n, writes U*; stage 2 reads
-# U*, U^n, writes U^{n+1}: 5 x 14 x 8 B.
-BYTES_PER_CELL_UPDATE = {"fp64": 560.0}
+# writes its output once):
+#   fp64 : stage 1 reads U^n, writes U*; stage 2 reads U*, U^n, writes
+#          U^{n+1}: 5 x 14 x 8 B = 560 B
+#   mixed: stage 1 reads W^n (FP32 primitives), writes W* (FP32); stage 2
+#          reads W*, U^n (FP64), W^n, writes U^{n+1} (FP64), W^{n+1}:
+#          (2 + 3) x 56 B + 2 x 112 B = 504 B
+BYTES_PER_CELL_UPDATE = {"fp64": 560.0, "mixed": 504.0}
+KERNEL = {"fp64": "mxe_stage14_2d_f64", "mixed": "mxe_stage14_2d_mixed"}
 
 
 def parse():
@@ -42,7 +47,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--n", type=int, default=4096)
-    p.add_argument("--precision", default="fp64", choices=["fp64"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--compare-steps", type=int, default=None,
+                   help="timed steps of the other precision (default: --steps)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -216,36 +223,49 @@ def main():
     n = args.n
     setup = wl.jets_setup(Kn=0.1)
     prim = np.ascontiguousarray(np.moveaxis(wl.jets_like_field(n, n, setup), -1, 0))
-    s = make_solver(mx, wl, n, args.precision, setup)
-    stream = torch.cuda.Stream()
-    s.set_stream(stream.cuda_stream)
-    s.set_state(prim)
     ncell = n * n
+    stream = torch.cuda.Stream()
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        s.step(1, float("inf"), sync=False)
-    barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    with ClockSampler(local) as clk:
+    def timed(precision, steps, sample_clocks):
+        s = make_solver(mx, wl, n, precision, setup)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(prim)
+        for _ in range(args.warmup):
+            s.step(1, float("inf"), sync=False)
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
         barrier()
         ev[0].record(stream)
-        for k in range(args.steps):
+        for k in range(steps):
             s.step(1, float("inf"), sync=False)
             ev[k + 1].record(stream)
         barrier()
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        if sampler:
+            sampler.__exit__()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return s, per, total_ms, sampler
+
+    s, per, total_ms, clk = timed(args.precision, args.steps, True)
     d = s.diagnostics()
     value = world * ncell * args.steps / (total_ms * 1e-3)
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    csteps = args.compare_steps or args.steps
+    s2, per2, total2, _ = timed(other, csteps, False)
+    other_value = world * ncell * csteps / (total2 * 1e-3)
+    del s2
 
     # end to end through the C-ABI with host buffers: H2D of the state,
     # one step, D2H of the state, every step
@@ -272,10 +292,13 @@ def main():
     bpc = BYTES_PER_CELL_UPDATE[args.precision]
     kt = statistics.mean(per) * 1e-3        # one step = both stage launches of the kernel
     achieved = bpc * ncell / kt / 1e9
+    bpc2 = BYTES_PER_CELL_UPDATE[other]
+    ach2 = bpc2 * ncell / (statistics.mean(per2) * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 (+f64 accumulator, f64 closure islands)",
         "data": "synthetic",
         "config": {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
                    "n": n, "precision": args.precision, "flux": "hll", "limiter": "minmod",
@@ -283,13 +306,20 @@ def main():
                    "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "kernel": "mxe_stage14_2d_f64", "peak_source": src,
+                     "kernel": KERNEL[args.precision], "peak_source": src,
                      "bytes_per_cell_update": bpc},
-        "gpu_launches": 2 * args.steps,
+        "compare": {"precision": other, "value": other_value, "unit": UNIT, "steps": csteps,
+                    "ms_per_step": total2 / csteps, "speedup_of_headline": value / other_value,
+                    "roofline": {"bound": "hbm", "achieved": ach2, "peak": hbm, "unit": "GB/s",
+                                 "frac": ach2 / hbm, "kernel": KERNEL[other],
+                                 "bytes_per_cell_update": bpc2}},
+        "gpu_launches": 2 * args.steps + (args.steps // 16 if args.precision == "mixed" else 0),
         "e2e": e2e,
         "clocks": clk.summary(),
         "diag": {"t": d["t"], "steps": d["steps"], "min_sigma": d["min_sigma"],
-                 "n_sigma_below_lim": d["n_sigma_below_lim"], "n_nonfinite": d["n_nonfinite"]},
+                 "n_sigma_below_lim": d["n_sigma_below_lim"], "n_nonfinite": d["n_nonfinite"],
+                 "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"])
+                 if d["n_closures"] else None},
     }
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl)

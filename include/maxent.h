@@ -90,8 +90,9 @@ typedef struct {
     long long n_sigma_above_one;/* cells with sigma > 1 (unrealizable)             */
     long long n_nonpositive;    /* cells with rho <= 0 or a non-positive pressure  */
     long long n_nonfinite;      /* cells with a non-finite conserved value         */
-    long long n_fp64_closures;  /* MIXED: face states evaluated in FP64 (last step)*/
-    long long n_closures;       /* MIXED: face states evaluated in total (last step)*/
+    long long n_fp64_closures;  /* MIXED: face states re-evaluated in FP64 since
+                                   mxe_set_state                                   */
+    long long n_closures;       /* MIXED: face states evaluated since mxe_set_state*/
     double    sums[14];         /* sum over cells of each conserved field          */
 } mxe_diag;
 
@@ -156,8 +157,17 @@ mxe_status mxe_step(mxe_ctx *ctx, int max_steps, double t_end, double *t_out,
  * of the CFL value (e.g. a recorded sequence). */
 mxe_status mxe_step_dt(mxe_ctx *ctx, int n, const double *dts);
 
-/* Diagnostics of the current state (synchronises).  dt_hist (may be NULL,
- * capacity n) receives the most recent time steps, oldest first. */
+/* MXE_MIXED only: which face states are re-evaluated in FP64 (raw sigma in
+ * [sigma_lim, sigma_lo) near the Junk subspace, sigma > sigma_hi near the
+ * realizability boundary, or det P* < det_min for an ill-conditioned
+ * pressure tensor; defaults 0 (off), 0.999, 1e-3) and how often (in steps)
+ * the FP32 primitive cache is re-derived from the FP64 conserved state
+ * (default 16).  det_min > 1 sends every face state to FP64 (det P* <= 1
+ * always, since tr P* = 3). */
+mxe_status mxe_set_mixed_policy(mxe_ctx *ctx, double sigma_lo, double sigma_hi,
+                                double det_min, int resync_every);
+
+/* Diagnostics of the current state (synchronises). */
 mxe_status mxe_get_diagnostics(mxe_ctx *ctx, mxe_diag *out);
 
 /* Last error message of the context (never NULL; "" if none). */

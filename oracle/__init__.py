@@ -110,6 +110,8 @@ def lib():
                              C.c_int, C.c_void_p]
         L.or_run.restype = C.c_int
         L.or_tau.argtypes = [C.POINTER(Cfg), _dp]; L.or_tau.restype = C.c_double
+        L.or_prim2cons_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_prim2cons_n.restype = None
+        L.or_cons2prim_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_cons2prim_n.restype = None
     return _lib
 
 
@@ -125,6 +127,23 @@ def prim2cons(Q):
     Q = _a(Q); U = np.empty_like(Q)
     (lib().or5_prim2cons if Q.size == 5 else lib().or14_prim2cons)(Q, U)
     return U
+
+
+def prim2cons_field(Q):
+    """(..., nf) primitive field -> conserved, cell by cell"""
+    Q = np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+    U = np.empty_like(Q)
+    nf = Q.shape[-1]
+    lib().or_prim2cons_n(nf, Q.size // nf, Q.reshape(-1), U.reshape(-1))
+    return U
+
+
+def cons2prim_field(U):
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.float64))
+    Q = np.empty_like(U)
+    nf = U.shape[-1]
+    lib().or_cons2prim_n(nf, U.size // nf, U.reshape(-1), Q.reshape(-1))
+    return Q
 
 
 def cons2prim(U):

@@ -501,6 +501,22 @@ void or14_source(const double *Q, double tau, double *C) {
     C[13] = -((4.0 * uPu + 4.0 * uq + R) - (4.0 * u2 * p + 15.0 * p * p / rho)) / tau;
 }
 
+/* Conversions of n cells (AoS, nf values per cell): plain loops over the
+ * point functions above. */
+void or_prim2cons_n(int nf, long n, const double *Q, double *U) {
+    for (long c = 0; c < n; ++c) {
+        if (nf == 5) or5_prim2cons(Q + c * 5, U + c * 5);
+        else or14_prim2cons(Q + c * 14, U + c * 14);
+    }
+}
+
+void or_cons2prim_n(int nf, long n, const double *U, double *Q) {
+    for (long c = 0; c < n; ++c) {
+        if (nf == 5) or5_cons2prim(U + c * 5, Q + c * 5);
+        else or14_cons2prim(U + c * 14, Q + c * 14);
+    }
+}
+
 /* ======================================================================= */
 /* finite-volume scheme, Sec. 3                                             */
 /* ======================================================================= */

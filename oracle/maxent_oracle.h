@@ -59,6 +59,10 @@ void   or14_wavespeeds(const double *Q, int dir, double sigma_lim, double k,
                        double *lmin, double *lmax);
 void   or14_source(const double *Q, double tau, double *C);
 
+/* bulk conversions of n cells (AoS) */
+void   or_prim2cons_n(int nf, long n, const double *Q, double *U);
+void   or_cons2prim_n(int nf, long n, const double *U, double *Q);
+
 /* ---------------- finite-volume scheme ---------------- */
 enum { OR_BC_TRANSMISSIVE = 0, OR_BC_PERIODIC = 1, OR_BC_DIRICHLET = 2 };
 enum { OR_FLUX_HLL = 0, OR_FLUX_RUSANOV = 1 };

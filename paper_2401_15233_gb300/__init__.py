@@ -23,7 +23,7 @@ __all__ = [
     "mxe_create", "mxe_destroy", "mxe_set_stream", "mxe_get_stream", "mxe_set_state",
     "mxe_get_moments", "mxe_set_bc", "mxe_set_relaxation", "mxe_step", "mxe_step_dt",
     "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
-    "mxe_batch_get_clock", "mxe_batch_run",
+    "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
@@ -101,6 +101,7 @@ def lib():
                                           C.c_double], C.c_int),
             "mxe_batch_get_clock": ([_P, _P, _P], C.c_int),
             "mxe_batch_run": ([_P, C.c_int, C.c_double], C.c_int),
+            "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -196,6 +197,10 @@ def mxe_last_error(ctx):
     return lib().mxe_last_error(ctx).decode()
 
 
+def mxe_set_mixed_policy(ctx, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
+    _check(ctx, lib().mxe_set_mixed_policy(ctx, sigma_lo, sigma_hi, det_min, resync_every))
+
+
 def mxe_batch_create(cfg: Config, ncells, lengths):
     nc = np.ascontiguousarray(np.asarray(ncells, dtype=np.int32))
     ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.float64))
@@ -289,6 +294,9 @@ class Solver:
 
     def diagnostics(self):
         return mxe_get_diagnostics(self.ctx)
+
+    def set_mixed_policy(self, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
+        mxe_set_mixed_policy(self.ctx, sigma_lo, sigma_hi, det_min, resync_every)
 
 
 class Batch(Solver):

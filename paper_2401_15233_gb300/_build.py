@@ -63,6 +63,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     def compile_one(src):
         obj = os.path.join(LIBDIR, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, "-c", src, "-o", obj] + flags(verbose)
+        if src.endswith("_mixed.cu"):
+            # FP32 stage arithmetic: approximate divisions/sqrt/transcendentals
+            # (MUFU); FP64 code in the same file is unaffected.
+            cmd += ["--use_fast_math"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

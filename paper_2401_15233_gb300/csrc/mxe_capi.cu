@@ -25,6 +25,14 @@ extern "C" __global__ void mxe_rate14_2d(const double* U, Grid2D g, SchemeParams
 extern "C" __global__ void mxe_tubes5_f64(const TubeArgs a);
 extern "C" __global__ void mxe_tubes14_f64(const TubeArgs a);
 size_t stage14_2d_f64_smem();
+struct MixedPolicy {
+    float sig_lo, sig_hi, det_min;
+};
+extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const MixedPolicy mp);
+extern "C" __global__ void mxe_resync14_2d(const double* U, float* W, Grid2D g);
+extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, SchemeParams sp,
+                                               DevClock* clk, int slot);
+size_t stage14_2d_mixed_smem();
 int tile_x();
 int tile_y();
 int tubes_threads();
@@ -61,6 +69,12 @@ struct mxe_ctx {
     // state
     double* U = nullptr;
     double* Us = nullptr;
+    float* W = nullptr;               // mixed: FP32 primitives of U
+    float* Ws = nullptr;              // mixed: FP32 primitives of the stage state
+    bool mixed = false;
+    MixedPolicy mp{0.0f, 0.999f, 1e-3f};
+    int resync_every = 16;
+    long long launched = 0;           // steps launched since set_state
     double* stage = nullptr;          // dense staging buffer (nf * ncell)
     double* dts_d = nullptr;          // prescribed dt sequence
     int dts_cap = 0;
@@ -140,8 +154,8 @@ static mxe_status check_cfg(mxe_ctx* c, const mxe_config* cfg, bool batch) {
         return fail(c, MXE_EINVAL, "the 5-moment (1D1V) system needs ny == 1");
     if (cfg->precision != MXE_FP64 && cfg->precision != MXE_MIXED)
         return fail(c, MXE_EINVAL, "precision must be MXE_FP64 or MXE_MIXED");
-    if (cfg->precision == MXE_MIXED)
-        return fail(c, MXE_EINVAL, "MXE_MIXED is not available in this build");
+    if (cfg->precision == MXE_MIXED && (batch || cfg->ny == 1 || cfg->system != 14))
+        return fail(c, MXE_EINVAL, "MXE_MIXED is available for 2D 14-moment grids");
     if (cfg->flux != MXE_FLUX_HLL && cfg->flux != MXE_FLUX_RUSANOV)
         return fail(c, MXE_EINVAL, "unknown flux %d", cfg->flux);
     if (cfg->limiter != MXE_LIM_MINMOD && cfg->limiter != MXE_LIM_VANALBADA)
@@ -160,9 +174,16 @@ static mxe_status alloc_common(mxe_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
     c->stream = c->own_stream;
     CK(cudaMalloc(&c->U, sizeof(double) * c->nelem));
-    CK(cudaMalloc(&c->Us, sizeof(double) * c->nelem));
     CK(cudaMemset(c->U, 0, sizeof(double) * c->nelem));
-    CK(cudaMemset(c->Us, 0, sizeof(double) * c->nelem));
+    if (c->mixed) {
+        CK(cudaMalloc(&c->W, sizeof(float) * c->nelem));
+        CK(cudaMalloc(&c->Ws, sizeof(float) * c->nelem));
+        CK(cudaMemset(c->W, 0, sizeof(float) * c->nelem));
+        CK(cudaMemset(c->Ws, 0, sizeof(float) * c->nelem));
+    } else {
+        CK(cudaMalloc(&c->Us, sizeof(double) * c->nelem));
+        CK(cudaMemset(c->Us, 0, sizeof(double) * c->nelem));
+    }
     CK(cudaMalloc(&c->stage, sizeof(double) * c->nf * c->ncell));
     CK(cudaMalloc(&c->scratch, sizeof(unsigned long long) * 8));
     CK(cudaMalloc(&c->accd, sizeof(double) * 32));
@@ -190,6 +211,7 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     }
     c->cfg = *cfg;
     c->nf = cfg->system;
+    c->mixed = cfg->precision == MXE_MIXED;
     if (cfg->ny == 1) {                 // 1D: a batch of one tube
         c->tubes = true;
         c->ntubes = 1;
@@ -209,6 +231,8 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
         c->g.fstride = (long long)c->g.pitch * cfg->ny;
         c->g.dx = (cfg->x1 - cfg->x0) / cfg->nx;
         c->g.dy = (cfg->y1 - cfg->y0) / cfg->ny;
+        c->g.idx = 1.0 / c->g.dx;
+        c->g.idy = 1.0 / c->g.dy;
         c->ncell = (long long)cfg->nx * cfg->ny;
         c->nelem = (long long)c->nf * c->g.fstride;
     }
@@ -232,9 +256,11 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     }
     c->g.ghost = c->ghost_d;
     if (!c->tubes) {
-        cudaError_t e = cudaFuncSetAttribute(mxe_stage14_2d_f64,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)stage14_2d_f64_smem());
+        cudaError_t e = c->mixed
+            ? cudaFuncSetAttribute(mxe_stage14_2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)stage14_2d_mixed_smem())
+            : cudaFuncSetAttribute(mxe_stage14_2d_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)stage14_2d_f64_smem());
         if (e != cudaSuccess) {
             fail(c, MXE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
             mxe_destroy(c);
@@ -302,6 +328,8 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->U);
     cudaFree(c->Us);
+    cudaFree(c->W);
+    cudaFree(c->Ws);
     cudaFree(c->stage);
     cudaFree(c->scratch);
     cudaFree(c->accd);
@@ -338,9 +366,15 @@ static mxe_status reset_clock(mxe_ctx* c) {
     }
     CK(cudaMemsetAsync(c->clk, 0, sizeof(DevClock), c->stream));
     c->slot = 0;
+    c->launched = 0;
     int nt = 256;
     dim3 grid((c->g.nx + nt - 1) / nt, c->g.ny);
-    mxe_rate14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
+    if (c->mixed) {
+        mxe_resync14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->W, c->g);
+        mxe_rate14_2d_mixed<<<grid, nt, 0, c->stream>>>(c->W, c->g, c->sp, c->clk, 0);
+    } else {
+        mxe_rate14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
+    }
     CK(cudaGetLastError());
     return MXE_OK;
 }
@@ -518,6 +552,29 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed) {
     a.slot = c->slot;
     a.clk = c->clk;
     dim3 grid((c->g.nx + tile_x() - 1) / tile_x(), (c->g.ny + tile_y() - 1) / tile_y());
+    if (c->mixed) {
+        size_t sm = stage14_2d_mixed_smem();
+        a.Ubase = c->U;
+        a.Uout = c->U;
+        if (c->cfg.integrator == MXE_RK2) {
+            a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
+            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+            a.Win = c->Ws; a.Wout = c->W; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
+            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+        } else {
+            a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
+            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+            std::swap(c->W, c->Ws);
+        }
+        CK(cudaGetLastError());
+        c->slot = (c->slot + 1) % 3;
+        if (++c->launched % c->resync_every == 0) {
+            dim3 rg((c->g.nx + 255) / 256, c->g.ny);
+            mxe_resync14_2d<<<rg, 256, 0, c->stream>>>(c->U, c->W, c->g);
+            CK(cudaGetLastError());
+        }
+        return MXE_OK;
+    }
     size_t smem = stage14_2d_f64_smem();
     if (c->cfg.integrator == MXE_RK2) {
         a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 0.5; a.final_stage = 0;
@@ -665,6 +722,18 @@ extern "C" mxe_status mxe_step_dt(mxe_ctx* c, int n, const double* dts) {
         s = launch_2d_step(c, INFINITY, dts[i]);
         if (s != MXE_OK) return s;
     }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_mixed_policy(mxe_ctx* c, double sigma_lo, double sigma_hi,
+                                           double det_min, int resync_every) {
+    if (!c) return MXE_EINVAL;
+    if (!c->mixed) return fail(c, MXE_ESTATE, "context is not MXE_MIXED");
+    if (!(std::isfinite(sigma_lo) && std::isfinite(sigma_hi) && std::isfinite(det_min)) ||
+        resync_every < 1)
+        return fail(c, MXE_EINVAL, "bad mixed-precision policy");
+    c->mp = MixedPolicy{(float)sigma_lo, (float)sigma_hi, (float)det_min};
+    c->resync_every = resync_every;
     return MXE_OK;
 }
 

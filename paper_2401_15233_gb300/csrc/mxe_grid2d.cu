@@ -122,9 +122,11 @@ __device__ __forceinline__ void riemann14(const T* QL, const T* QR, const Scheme
 #pragma unroll
         for (int k = 0; k < 14; ++k) Fo[k] = FR[k];
     } else {
+        T inv = T(1) / (SR - SL);
+        T SLR = SL * SR;
 #pragma unroll
         for (int k = 0; k < 14; ++k)
-            Fo[k] = (SR * FL[k] - SL * FR[k] + SL * SR * (UR[k] - UL[k])) / (SR - SL);
+            Fo[k] = (SR * FL[k] - SL * FR[k] + SLR * (UR[k] - UL[k])) * inv;
     }
 }
 
@@ -188,8 +190,14 @@ mxe_stage14_2d_f64(const Stage2DArgs a) {
     double* red = phy + NPHY;                        // [8]
 
     const int tid = threadIdx.x;
-    double t;
-    const double dt = step_dt(a.clk, a.slot, a.cfl, a.t_end, a.dt_fixed, t);
+    __shared__ double sdt[2];
+    if (tid == 0) {
+        double tt;
+        sdt[0] = step_dt(a.clk, a.slot, a.cfl, a.t_end, a.dt_fixed, tt);
+        sdt[1] = tt;
+    }
+    __syncthreads();
+    const double dt = sdt[0], t = sdt[1];
     if (a.final_stage && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;
         a.clk->rate[s2] = 0ull;
@@ -255,7 +263,7 @@ mxe_stage14_2d_f64(const Stage2DArgs a) {
         }
 #pragma unroll
         for (int k = 0; k < 14; ++k)
-            L[k] -= (Fb[k * NT2 + cy * 16 + cx + 1] - Fb[k * NT2 + cy * 16 + cx]) / g.dx;
+            L[k] -= (Fb[k * NT2 + cy * 16 + cx + 1] - Fb[k * NT2 + cy * 16 + cx]) * g.idx;
     }
     __syncthreads();
     // ---- y faces: face fy in [0,17) of column cx, between box rows fy+1 | fy+2
@@ -275,7 +283,7 @@ mxe_stage14_2d_f64(const Stage2DArgs a) {
     if (owner) {
 #pragma unroll
         for (int k = 0; k < 14; ++k)
-            L[k] -= (Fb[k * NT2 + (cy + 1) * TX + cx] - Fb[k * NT2 + cy * TX + cx]) / g.dy;
+            L[k] -= (Fb[k * NT2 + (cy + 1) * TX + cx] - Fb[k * NT2 + cy * TX + cx]) * g.idy;
         int gi = i0 + cx, gj = j0 + cy;
         if (gi < g.nx && gj < g.ny) {
             long long o = (long long)gj * g.pitch + gi;
@@ -299,8 +307,8 @@ mxe_stage14_2d_f64(const Stage2DArgs a) {
                 dimless14(Qn, d);
                 double ax = amax14<double, 0>(Qn, d, a.sp);
                 double ay = amax14<double, 1>(Qn, d, a.sp);
-                r = ax / g.dx;
-                r = r + ay / g.dy;
+                r = ax * g.idx;
+                r = r + ay * g.idy;
                 if (!(r >= 0.0)) r = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> inf
             }
         }

@@ -38,6 +38,7 @@ struct Grid2D {
     int nx, ny, pitch;              // pitch: row stride in elements
     long long fstride;              // field stride (ny * pitch)
     double dx, dy;
+    double idx, idy;                // 1/dx, 1/dy
     SideDesc side[4];
     const double* ghost;            // [4][GHOST_SLOTS][14] primitive ghost states
 };

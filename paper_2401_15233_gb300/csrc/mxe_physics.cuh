@@ -306,7 +306,7 @@ __device__ __forceinline__ void sym_mul(const T* A, const T* B, T* C) {
 }
 
 template <class T>
-__device__ __forceinline__ void sym_inv(const T* A, T* I) {
+__device__ __forceinline__ T sym_inv(const T* A, T* I) {
     T c00 = A[3] * A[5] - A[4] * A[4];
     T c01 = A[2] * A[4] - A[1] * A[5];
     T c02 = A[1] * A[4] - A[2] * A[3];
@@ -318,6 +318,7 @@ __device__ __forceinline__ void sym_inv(const T* A, T* I) {
     I[3] = (A[0] * A[5] - A[2] * A[2]) * id;
     I[4] = (A[1] * A[2] - A[0] * A[4]) * id;
     I[5] = (A[0] * A[3] - A[1] * A[1]) * id;
+    return det;
 }
 
 template <class T>
@@ -337,6 +338,7 @@ struct Dimless14 {
     T Pi[6];           // P*^-1
     T y[3];            // P*^-1 q*
     T sig;             // raw sigma
+    T det;             // det P* (<= 1 since tr P* = 3; small = ill-conditioned)
 };
 
 template <class T>
@@ -355,13 +357,34 @@ __device__ __forceinline__ void dimless14(const T* Q, Dimless14<T>& d) {
     d.trPs = d.Ps[0] + d.Ps[3] + d.Ps[5];
     d.T2 = d.Ps[0] * d.Ps[0] + d.Ps[3] * d.Ps[3] + d.Ps[5] * d.Ps[5]
          + T(2) * (d.Ps[1] * d.Ps[1] + d.Ps[2] * d.Ps[2] + d.Ps[4] * d.Ps[4]);
-    sym_inv(d.Ps, d.Pi);
+    d.det = sym_inv(d.Ps, d.Pi);
     sym_vec(d.Pi, d.qs, d.y);
     T qPq = d.qs[0] * d.y[0] + d.qs[1] * d.y[1] + d.qs[2] * d.y[2];
     T A = T(2) * d.T2 + d.trPs * d.trPs - Rs;
     T X = T(8) * d.T2 * qPq;
     d.sig = sigma_root(A, X, d.T2);
 }
+
+// B = 5 - 4 sqrt(s) + sqrt(10 - 16 sqrt(s) + 6 s) and Y = B + E^2 - 2 E sqrt(B)
+// of the wave-speed fits.  Double: as printed.  Float: the algebraically
+// identical 10 - 16 r + 6 r^2 = 2 (5 - 3 r)(1 - r) (r = sqrt s) and
+// Y = (sqrt B - E)^2, which keep their digits as sigma -> 1.
+template <class T> struct WsTerms;
+template <> struct WsTerms<double> {
+    static __device__ __forceinline__ void get(double ssb, double sb, double E, double& B,
+                                               double& Y) {
+        B = 5.0 - 4.0 * ssb + ::sqrt(10.0 - 16.0 * ssb + 6.0 * sb);
+        Y = B + E * E - 2.0 * E * ::sqrt(B);
+    }
+};
+template <> struct WsTerms<float> {
+    static __device__ __forceinline__ void get(float ssb, float sb, float E, float& B,
+                                               float& Y) {
+        B = 5.0f - 4.0f * ssb + ::sqrtf(2.0f * (5.0f - 3.0f * ssb) * (1.0f - ssb));
+        float d = ::sqrtf(B) - E;
+        Y = d * d;
+    }
+};
 
 // Eq. (14mom-approx-ws-equations): lambda*_max and lambda*_min along k.
 template <class T, int K>
@@ -376,8 +399,8 @@ __device__ __forceinline__ void lam14_star(const Dimless14<T>& d, T sb, T& lp, T
     T ssb = M<T>::sqrt_(sb);
     T C = M<T>::sqrt_((T(3) - T(3) * sb) * Pkk);
     T E = T(0.8) * C;
-    T B = T(5) - T(4) * ssb + M<T>::sqrt_(T(10) - T(16) * ssb + T(6) * sb);
-    T Y = B + E * E - T(2) * E * M<T>::sqrt_(B);
+    T B, Y;
+    WsTerms<T>::get(ssb, sb, E, B, Y);
     T al = qperp * (T(0.6) * Pkk * Pkk - T(0.38) * Pkk + T(0.35));
     T base = T(4) * sb * sb * Y + qperp * qperp / T(10);
     T pre = (a * sb + b) / (T(2) * sb);
@@ -509,6 +532,66 @@ __device__ __forceinline__ T amax14(const T* Q, const Dimless14<T>& d, const Sch
     T lmin = Q[1 + K] + k * lm * d.sq;
     T a = fabs(lmin), b = fabs(lmax);
     return a > b ? a : b;
+}
+
+// Primitive moments of cons(W) + dU from the increment alone (FP32 path):
+// every term below is proportional to the increment, so nothing of the size
+// of the bulk-motion contributions (rho u^4 against R at high Mach number)
+// is cancelled.  Algebraically W' = prim(cons(W) + dU) exactly.
+__device__ __forceinline__ void prim_increment14(const float* W, const float* dU, float* Wn) {
+    float rho = W[0];
+    float u[3] = {W[1], W[2], W[3]};
+    const float* P = W + 4;
+    const float* q = W + 10;
+    float drho = dU[0];
+    float rho1 = rho + drho;
+    float ir1 = 1.0f / rho1;
+    float du[3], u1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        du[i] = (dU[1 + i] - u[i] * drho) * ir1;
+        u1[i] = u[i] + du[i];
+    }
+    float dP[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+            dP[sidx(a, b)] = dU[4 + sidx(a, b)] - drho * u[a] * u[b]
+                           - rho1 * (u[a] * du[b] + du[a] * u[b] + du[a] * du[b]);
+    float P1[6];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) P1[n] = P[n] + dP[n];
+    float trP1 = P1[0] + P1[3] + P1[5];
+    float dtr = dP[0] + dP[3] + dP[5];
+    float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    float s = 2.0f * (u[0] * du[0] + u[1] * du[1] + u[2] * du[2])
+            + (du[0] * du[0] + du[1] * du[1] + du[2] * du[2]);
+    float Pdu[3], dPu1[3], Pu[3];
+    sym_vec(P, du, Pdu);
+    sym_vec(dP, u1, dPu1);
+    sym_vec(P, u, Pu);
+    float q1[3], dq[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float dG = drho * u[i] * u2 + rho1 * (du[i] * u2 + u1[i] * s) + du[i] * trP1 + u[i] * dtr
+                 + 2.0f * (dPu1[i] + Pdu[i]);
+        dq[i] = dU[10 + i] - dG;
+        q1[i] = q[i] + dq[i];
+    }
+    float u1dPu1 = u1[0] * dPu1[0] + u1[1] * dPu1[1] + u1[2] * dPu1[2];
+    float duPu = du[0] * Pu[0] + du[1] * Pu[1] + du[2] * Pu[2];
+    float duPdu = du[0] * Pdu[0] + du[1] * Pdu[1] + du[2] * Pdu[2];
+    float dK = drho * u2 * u2 + rho1 * s * (2.0f * u2 + s) + 2.0f * (s * trP1 + u2 * dtr)
+             + 4.0f * (u1dPu1 + 2.0f * duPu + duPdu)
+             + 4.0f * (du[0] * q1[0] + du[1] * q1[1] + du[2] * q1[2]
+                       + u[0] * dq[0] + u[1] * dq[1] + u[2] * dq[2]);
+    Wn[0] = rho1;
+    Wn[1] = u1[0]; Wn[2] = u1[1]; Wn[3] = u1[2];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) Wn[4 + n] = P1[n];
+    Wn[10] = q1[0]; Wn[11] = q1[1]; Wn[12] = q1[2];
+    Wn[13] = W[13] + (dU[13] - dK);
 }
 
 // BGK sources of Sec. 2.4.

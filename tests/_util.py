@@ -21,23 +21,11 @@ def soa_to_aos(U):
 
 def cons_field(orc, prim):
     """primitive (..., nf) -> conserved via the oracle, cell by cell"""
-    sh = prim.shape
-    flat = prim.reshape(-1, sh[-1])
-    f = orc.lib().or14_prim2cons if sh[-1] == 14 else orc.lib().or5_prim2cons
-    out = np.empty_like(flat)
-    for n in range(flat.shape[0]):
-        f(flat[n], out[n])
-    return out.reshape(sh)
+    return orc.prim2cons_field(prim)
 
 
 def prim_field(orc, U):
-    sh = U.shape
-    flat = np.ascontiguousarray(U.reshape(-1, sh[-1]))
-    f = orc.lib().or14_cons2prim if sh[-1] == 14 else orc.lib().or5_cons2prim
-    out = np.empty_like(flat)
-    for n in range(flat.shape[0]):
-        f(flat[n], out[n])
-    return out.reshape(sh)
+    return orc.cons2prim_field(U)
 
 
 def field_rel_err(a, b, axis_field=-1):

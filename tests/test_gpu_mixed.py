@@ -1,0 +1,181 @@
+"""Mixed precision (FP32 stage arithmetic, FP64 conserved accumulator, FP64
+closure where ill-conditioned) against the FP64 oracle.
+
+Bounds (stated before measuring): the per-field L1 error of a mixed run
+after N steps must stay within 10x the L1 difference between two FP64 oracle
+runs whose data (initial state and inflow states) differ by a 1e-7 relative
+perturbation -- the problem's own sensitivity to data at FP32 resolution."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2401_15233_gb300 import workloads as wl
+from tests._util import aos_to_soa, cons_field, field_rel_err, jets_gpu_solver, jets_oracle_cfg, soa_to_aos
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_15233_gb300 as m
+    m.lib()
+    return m
+
+
+def l1_rel(a, b):
+    a = a.reshape(-1, a.shape[-1]); b = b.reshape(-1, b.shape[-1])
+    den = np.abs(b).sum(0)
+    return np.abs(a - b).sum(0) / np.where(den > 0, den, 1.0)
+
+
+def step_sensitivity(orc, cfg, U, dt, rng):
+    """Per-field normwise change of one FP64 oracle step when every primitive
+    of the input is perturbed by 1e-7 relative (the data resolution of FP32)."""
+    prim = orc.cons2prim_field(U)
+    Up = orc.prim2cons_field(prim * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=prim.shape)))
+    return field_rel_err(orc.step(cfg, Up, dt), orc.step(cfg, U, dt))
+
+
+POLICIES = {"off": (0.0, 2.0, 0.0), "default": (0.0, 0.999, 1e-3),
+            "wide": (1e-2, 0.99, 1e-2), "all": (0.0, 0.0, 2.0)}
+
+
+@pytest.mark.parametrize("policy", list(POLICIES))
+def test_mixed_per_step_error_by_policy(mx, orc, policy):
+    """One mixed step from the oracle's state, for each FP64-closure policy:
+    the error (FP32 arithmetic through the whole stage) is reported next to
+    the step's sensitivity to a 1e-7 data perturbation, and bounded by 1e-4
+    (a per-step sanity bound; the accuracy gate is the multi-step L1 test)."""
+    n = 48
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(11)
+    prim = wl.jets_like_field(n, n, setup)
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+    s.set_mixed_policy(*POLICIES[policy], resync_every=16)
+    U = cons_field(orc, prim)
+    worst, sens_min = np.zeros(14), np.full(14, np.inf)
+    for k in range(4):
+        dt = orc.dt(cfg, U, 0.0, 10.0)
+        U1 = orc.step(cfg, U, dt)
+        sens = step_sensitivity(orc, cfg, U, dt, rng)
+        s.set_state(aos_to_soa(U), kind="conserved")
+        s.step_dt([dt])
+        e = field_rel_err(soa_to_aos(s.get_moments("conserved")), U1)
+        assert e.max() <= 1e-4, (k, e, sens)
+        worst = np.maximum(worst, e)
+        sens_min = np.minimum(sens_min, sens)
+        U = U1
+    d = s.diagnostics()
+    print(f"policy {policy}: mixed per-step error max {worst.max():.2e} "
+          f"(sensitivity min {sens_min[sens_min > 0].min():.2e}); "
+          f"FP64 closures {d['n_fp64_closures']} of {d['n_closures']}")
+    if policy == "all":
+        assert d["n_fp64_closures"] == d["n_closures"] > 0
+    if policy == "off":
+        assert d["n_fp64_closures"] == 0
+
+
+def test_mixed_l1_within_sensitivity_bound(mx, orc):
+    n, t_end = 64, 6e-3
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(99)
+    prim = wl.jets_like_field(n, n, setup)
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    A, ta, ha = orc.run(cfg, cons_field(orc, prim), 0.0, t_end, 10 ** 5)
+    # perturbed data: every primitive of the initial state and of both inflow states
+    pert = lambda x: x * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=np.shape(x)))
+    # inflow: Maxwellians with perturbed density, speed and temperature
+    a = math.sqrt(wl.GAMMA_3D)
+    r1, u1, T1 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    r2, u2, T2 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    setup_p = dict(setup, left=wl.maxwellian14(r1, u1, 0.0, T1),
+                   bottom=wl.maxwellian14(r2, 0.0, u2, T2))
+    prim_p = pert(prim)
+    cfg_p = jets_oracle_cfg(orc, n, n, setup_p)
+    B, tb, hb = orc.run(cfg_p, cons_field(orc, prim_p), 0.0, t_end, 10 ** 5)
+    sens = l1_rel(B, A)
+    bound = np.maximum(10 * sens, 1e-10)
+    s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+    s.set_state(aos_to_soa(prim))
+    tg, ng = s.step(10 ** 5, t_end)
+    G = soa_to_aos(s.get_moments("conserved"))
+    e_mixed = l1_rel(G, A)
+    s64 = jets_gpu_solver(mx, n, n, setup, precision="fp64")
+    s64.set_state(aos_to_soa(prim))
+    s64.step(10 ** 5, t_end)
+    e_fp64 = l1_rel(soa_to_aos(s64.get_moments("conserved")), A)
+    print("steps oracle/mixed", len(ha), ng)
+    print("sensitivity (1e-7 data perturbation) L1:", sens)
+    print("mixed L1:", e_mixed)
+    print("fp64 GPU L1:", e_fp64)
+    assert tg == pytest.approx(t_end, rel=1e-12)
+    nz = np.abs(A.reshape(-1, 14)).sum(0) > 0
+    assert np.all(e_mixed[nz] <= bound[nz]), (e_mixed, bound)
+
+
+def test_mixed_conservation_periodic(mx, orc):
+    """Mass, momentum and energy drift of the mixed path under periodic BCs:
+    the FP64 accumulator adds FP32 increments, so the telescoping sum is exact
+    only to FP32 rounding of each increment (reported and bounded)."""
+    nx, ny = 64, 48
+    rng = np.random.default_rng(5)
+    prim = wl.smooth_field14(rng, nx, ny, amp=0.4)
+    s = mx.Solver(system=14, nx=nx, ny=ny, precision="mixed")
+    for side in range(4):
+        s.set_bc(side, mx.BC_PERIODIC)
+    s.set_relaxation(mx.TAU_CONST, 0.05)
+    s.set_state(aos_to_soa(prim))
+    d0 = s.diagnostics()
+    s.step(200, 10.0)
+    d1 = s.diagnostics()
+    rel = [abs(d1["sums"][k] - d0["sums"][k]) / abs(d0["sums"][0]) for k in range(4)]
+    e0 = d0["sums"][4] + d0["sums"][7] + d0["sums"][9]
+    e1 = d1["sums"][4] + d1["sums"][7] + d1["sums"][9]
+    rel.append(abs(e1 - e0) / abs(e0))
+    print("mixed conservation drift over 200 steps", rel)
+    # mass and momentum increments telescope to FP32 rounding of each face
+    # difference; the energy trace also collects the FP32 rounding of the
+    # traceless BGK source (tau = 0.05 here, a fast relaxation)
+    assert max(rel[:4]) <= 1e-10 and rel[4] <= 1e-7
+
+
+def test_mixed_sampled_4096_bench_config(mx, orc):
+    """Bench workload (4096^2), one mixed step, sampled windows against the
+    oracle, within 10x the windows' per-step data sensitivity (errors and
+    sensitivities floored by each field's RMS over the grid)."""
+    n = 4096
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(4096)
+    prim = wl.jets_like_field(n, n, setup)
+    Ufull = cons_field(orc, prim)
+    s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+    s.set_state(aos_to_soa(Ufull), kind="conserved")
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    sub = Ufull[::64, ::64]
+    rms = np.sqrt((sub.reshape(-1, 14) ** 2).mean(axis=0))
+    dt = 2.5e-8
+    s.step_dt([dt])
+    G = s.get_moments("conserved")
+    for (i0, j0, w, h) in [(0, 1843, 16, 24), (1843, 0, 24, 16), (2040, 2040, 16, 16),
+                           (4080, 4080, 16, 16), (2900, 2050, 15, 16)]:
+        M = 4
+        ii = np.clip(np.arange(i0 - M, i0 + w + M), 0, n - 1)
+        jj = np.clip(np.arange(j0 - M, j0 + h + M), 0, n - 1)
+        Ub = np.ascontiguousarray(Ufull[np.ix_(jj, ii)])
+        pb = orc.cons2prim_field(Ub)
+        Ubp = orc.prim2cons_field(pb * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=pb.shape)))
+        ref = orc.block_step(cfg, i0, j0, w, h, Ub, dt).reshape(-1, 14)
+        refp = orc.block_step(cfg, i0, j0, w, h, Ubp, dt).reshape(-1, 14)
+        got = soa_to_aos(G[:, j0:j0 + h, i0:i0 + w]).reshape(-1, 14)
+        den = np.maximum(np.linalg.norm(ref, axis=0), rms * math.sqrt(w * h))
+        ok = den > 0
+        e = np.linalg.norm(got - ref, axis=0)[ok] / den[ok]
+        sens = np.linalg.norm(refp - ref, axis=0)[ok] / den[ok]
+        print(f"window {(i0, j0)}: mixed {e.max():.2e}, sensitivity {sens.max():.2e}")
+        assert np.all(e <= 10 * np.maximum(sens, 1e-12)), ((i0, j0), e, sens)
+        assert np.all(np.linalg.norm(got, axis=0)[~ok] == 0)
