@@ -195,6 +195,41 @@ mxe_status mxe_batch_get_clock(mxe_ctx *ctx, double *t, long long *steps);
  * max_steps steps in this call; one launch for the whole batch. */
 mxe_status mxe_batch_run(mxe_ctx *ctx, int max_steps, double t_end);
 
+/* ---- fixed-scratch 1D solve (allocates nothing) -------------------------- */
+
+/* No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory -- a host program whose device memory is
+ * wholly owned by its own pool allocator (an outside cudaMalloc fails under
+ * the pool's cap or breaks its accounting), or a time-critical loop that
+ * cannot pay for cudaMalloc/cudaFree, which synchronise the device.
+ *
+ * Advances one 1D problem (cfg->ny == 1, cfg->nx <= 16384 cells, FP64) with
+ * the same persistent kernel as mxe_step, from time t0 until t_end or
+ * max_steps steps.  U is a device array of nf*nx doubles (conserved SoA,
+ * field-major), read and overwritten in place; the caller owns it.  BCs are
+ * transmissive or periodic (bc_lo, bc_hi); relaxation as in
+ * mxe_set_relaxation.  Every other buffer (stage buffer, descriptor, clock)
+ * is a fixed file-scope device array of the library: 1.75 MiB plus a few
+ * hundred bytes, held on every GPU that loads the library until the process
+ * exits.  No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ *  - The first call on a device looks up the arrays' device addresses
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the arrays, which keep the last call's contents; the
+ *    clock is re-initialised by every call.  Calls that overlap on the GPU
+ *    (other streams, other host threads) race on the shared arrays and must
+ *    be serialised by the caller.
+ *  - t_out / steps_out (host, may be NULL) receive the final time and the
+ *    steps taken; passing either synchronises `stream` (a cudaStream_t, NULL
+ *    for the default stream).
+ * Returns MXE_EINVAL for nx > 16384 or any other invalid argument, before
+ * any device work. */
+mxe_status mxe_tube_run_noalloc(const mxe_config *cfg, int bc_lo, int bc_hi, int tau_model,
+                                double tau_ref, double rho_ref, double T_ref, double *U,
+                                double t0, double t_end, int max_steps, double *t_out,
+                                int *steps_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

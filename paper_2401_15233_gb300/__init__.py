@@ -23,7 +23,7 @@ __all__ = [
     "mxe_create", "mxe_destroy", "mxe_set_stream", "mxe_get_stream", "mxe_set_state",
     "mxe_get_moments", "mxe_set_bc", "mxe_set_relaxation", "mxe_step", "mxe_step_dt",
     "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
-    "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy",
+    "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy", "mxe_tube_run_noalloc",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
@@ -102,6 +102,10 @@ def lib():
             "mxe_batch_get_clock": ([_P, _P, _P], C.c_int),
             "mxe_batch_run": ([_P, C.c_int, C.c_double], C.c_int),
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
+            "mxe_tube_run_noalloc": ([C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_double,
+                                      C.c_double, C.c_double, _P, C.c_double, C.c_double,
+                                      C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int), _P],
+                                     C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -199,6 +203,24 @@ def mxe_last_error(ctx):
 
 def mxe_set_mixed_policy(ctx, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
     _check(ctx, lib().mxe_set_mixed_policy(ctx, sigma_lo, sigma_hi, det_min, resync_every))
+
+
+def mxe_tube_run_noalloc(cfg: Config, U_dev, t0, t_end, max_steps, bc_lo=BC_TRANSMISSIVE,
+                         bc_hi=BC_TRANSMISSIVE, tau_model=TAU_NONE, tau_ref=1.0, rho_ref=1.0,
+                         T_ref=1.0, stream=None):
+    """1D solve on a caller-owned device array (torch CUDA float64 tensor,
+    conserved SoA (nf, nx)) using only the library's fixed device arrays."""
+    p, dev = _ptr(U_dev)
+    if not dev:
+        raise ValueError("U must be a device tensor")
+    t = C.c_double()
+    n = C.c_int()
+    st = lib().mxe_tube_run_noalloc(C.byref(cfg), bc_lo, bc_hi, tau_model, tau_ref, rho_ref,
+                                    T_ref, p, t0, t_end, max_steps, C.byref(t), C.byref(n),
+                                    _P(stream) if stream else None)
+    if st != OK:
+        raise MaxentError(st, "mxe_tube_run_noalloc failed")
+    return t.value, n.value
 
 
 def mxe_batch_create(cfg: Config, ncells, lengths):
