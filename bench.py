@@ -37,8 +37,12 @@ UNIT = "cell-updates/s"
 #   mixed: stage 1 reads W^n (FP32 primitives), writes W* (FP32); stage 2
 #          reads W*, U^n (FP64), W^n, writes U^{n+1} (FP64), W^{n+1}:
 #          (2 + 3) x 56 B + 2 x 112 B = 504 B
-BYTES_PER_CELL_UPDATE = {"fp64": 560.0, "mixed": 504.0}
-KERNEL = {"fp64": "mxe_stage14_2d_f64", "mixed": "mxe_stage14_2d_mixed"}
+#   planar states (u_z, P_xz, P_yz, q_z identically zero, as in the crossed
+#   jets): ten fields instead of fourteen -> fp64 400 B, mixed 360 B
+BYTES_PER_CELL_UPDATE = {("fp64", False): 560.0, ("mixed", False): 504.0,
+                         ("fp64", True): 400.0, ("mixed", True): 360.0}
+KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed",
+          ("fp64", True): "mxe_stage14_2d_f64_planar", ("mixed", True): "mxe_stage14_2d_mixed_planar"}
 
 
 def parse():
@@ -260,11 +264,13 @@ def main():
 
     s, per, total_ms, clk = timed(args.precision, args.steps, True)
     d = s.diagnostics()
+    planar = bool(d["planar"])
     value = world * ncell * args.steps / (total_ms * 1e-3)
     other = "fp64" if args.precision == "mixed" else "mixed"
     csteps = args.compare_steps or args.steps
     s2, per2, total2, _ = timed(other, csteps, False)
     other_value = world * ncell * csteps / (total2 * 1e-3)
+    planar2 = bool(s2.diagnostics()["planar"])
     del s2
 
     # end to end through the C-ABI with host buffers: H2D of the state,
@@ -289,10 +295,10 @@ def main():
     if rank != 0:
         return
     hbm, src = peaks()
-    bpc = BYTES_PER_CELL_UPDATE[args.precision]
+    bpc = BYTES_PER_CELL_UPDATE[(args.precision, planar)]
     kt = statistics.mean(per) * 1e-3        # one step = both stage launches of the kernel
     achieved = bpc * ncell / kt / 1e9
-    bpc2 = BYTES_PER_CELL_UPDATE[other]
+    bpc2 = BYTES_PER_CELL_UPDATE[(other, planar2)]
     ach2 = bpc2 * ncell / (statistics.mean(per2) * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -302,16 +308,16 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
                    "n": n, "precision": args.precision, "flux": "hll", "limiter": "minmod",
-                   "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}",
+                   "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
                    "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "kernel": KERNEL[args.precision], "peak_source": src,
+                     "kernel": KERNEL[(args.precision, planar)], "peak_source": src,
                      "bytes_per_cell_update": bpc},
         "compare": {"precision": other, "value": other_value, "unit": UNIT, "steps": csteps,
                     "ms_per_step": total2 / csteps, "speedup_of_headline": value / other_value,
                     "roofline": {"bound": "hbm", "achieved": ach2, "peak": hbm, "unit": "GB/s",
-                                 "frac": ach2 / hbm, "kernel": KERNEL[other],
+                                 "frac": ach2 / hbm, "kernel": KERNEL[(other, planar2)],
                                  "bytes_per_cell_update": bpc2}},
         "gpu_launches": 2 * args.steps + (args.steps // 16 if args.precision == "mixed" else 0),
         "e2e": e2e,

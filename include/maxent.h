@@ -94,6 +94,10 @@ typedef struct {
                                    mxe_set_state                                   */
     long long n_closures;       /* MIXED: face states evaluated since mxe_set_state*/
     double    sums[14];         /* sum over cells of each conserved field          */
+    long long planar;           /* 1 if the 2D 14-moment state is planar (u_z,
+                                   P_xz, P_yz, q_z zero in the state and all
+                                   boundary states): those moments stay zero
+                                   and are neither stored nor computed        */
 } mxe_diag;
 
 typedef struct mxe_ctx mxe_ctx;

@@ -56,6 +56,7 @@ class Diag(C.Structure):
         ("n_nonpositive", C.c_longlong), ("n_nonfinite", C.c_longlong),
         ("n_fp64_closures", C.c_longlong), ("n_closures", C.c_longlong),
         ("sums", C.c_double * 14),
+        ("planar", C.c_longlong),
     ]
 
     def as_dict(self):

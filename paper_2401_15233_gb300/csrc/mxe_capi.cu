@@ -17,28 +17,41 @@
 #include "../../include/maxent.h"
 #include "mxe_internal.h"
 
+#include "mxe_policy.cuh"
+
 namespace mxe {
 // kernels defined in the other translation units
 extern "C" __global__ void mxe_stage14_2d_f64(const Stage2DArgs a);
+extern "C" __global__ void mxe_stage14_2d_f64_planar(const Stage2DArgs a);
 extern "C" __global__ void mxe_rate14_2d(const double* U, Grid2D g, SchemeParams sp,
                                          DevClock* clk, int slot);
+extern "C" __global__ void mxe_rate14_2d_planar(const double* U, Grid2D g, SchemeParams sp,
+                                                DevClock* clk, int slot);
 extern "C" __global__ void mxe_tubes5_f64(const TubeArgs a);
 extern "C" __global__ void mxe_tubes14_f64(const TubeArgs a);
-size_t stage14_2d_f64_smem();
+size_t stage14_2d_f64_smem(bool planar);
 struct MixedPolicy {
     float sig_lo, sig_hi, det_min;
 };
-extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const MixedPolicy mp);
+extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const ParamsT<float> p,
+                                                const MixedPolicy mp);
+extern "C" __global__ void mxe_stage14_2d_mixed_planar(const Stage2DArgs a,
+                                                       const ParamsT<float> p,
+                                                       const MixedPolicy mp);
 extern "C" __global__ void mxe_resync14_2d(const double* U, float* W, Grid2D g);
-extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, SchemeParams sp,
-                                               DevClock* clk, int slot);
-size_t stage14_2d_mixed_smem();
+extern "C" __global__ void mxe_resync14_2d_planar(const double* U, float* W, Grid2D g);
+extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, ParamsT<float> p,
+                                               float idxf, float idyf, DevClock* clk, int slot);
+extern "C" __global__ void mxe_rate14_2d_mixed_planar(const float* W, Grid2D g,
+                                                      ParamsT<float> p, float idxf, float idyf,
+                                                      DevClock* clk, int slot);
+size_t stage14_2d_mixed_smem(bool planar);
 int tile_x();
 int tile_y();
 int tubes_threads();
 
 extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
-                                          unsigned long long* bad);
+                                          unsigned long long* bad, unsigned* nonplanar);
 extern "C" __global__ void mxe_k_setstate(CellMap m, int nf, int kind, const double* src,
                                           double* U);
 extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const double* U,
@@ -75,6 +88,8 @@ struct mxe_ctx {
     MixedPolicy mp{0.0f, 0.999f, 1e-3f};
     int resync_every = 16;
     long long launched = 0;           // steps launched since set_state
+    bool state_planar = false;        // z-odd moments exactly zero (and kept so)
+    bool w_planar = false;            // layout of W (mixed): compact planar fields
     double* stage = nullptr;          // dense staging buffer (nf * ncell)
     double* dts_d = nullptr;          // prescribed dt sequence
     int dts_cap = 0;
@@ -258,9 +273,16 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     if (!c->tubes) {
         cudaError_t e = c->mixed
             ? cudaFuncSetAttribute(mxe_stage14_2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)stage14_2d_mixed_smem())
+                                   (int)stage14_2d_mixed_smem(false))
             : cudaFuncSetAttribute(mxe_stage14_2d_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)stage14_2d_f64_smem());
+                                   (int)stage14_2d_f64_smem(false));
+        if (e == cudaSuccess)
+            e = c->mixed ? cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)stage14_2d_mixed_smem(true))
+                         : cudaFuncSetAttribute(mxe_stage14_2d_f64_planar,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)stage14_2d_f64_smem(true));
         if (e != cudaSuccess) {
             fail(c, MXE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
             mxe_destroy(c);
@@ -354,6 +376,37 @@ extern "C" void* mxe_get_stream(const mxe_ctx* c) { return c ? (void*)c->stream 
 
 extern "C" const char* mxe_last_error(const mxe_ctx* c) { return c ? c->err.c_str() : ""; }
 
+// ---------------------------------------------------------------- planar states
+// The z-odd moments (u_z, P_xz, P_yz, q_z) of a 14-moment 2D state stay
+// exactly zero when they are zero initially and in every boundary state;
+// the planar kernels then carry the ten remaining moments only.
+static bool bc_planar(const mxe_ctx* c) {
+    const int zodd[4] = {3, 6, 8, 12};
+    for (int s = 0; s < 4; ++s)
+        for (int n = 0; n < GHOST_SLOTS; ++n) {
+            bool used = (n == 0 && c->bc_type[s] == MXE_BC_DIRICHLET) || (n > 0 && n <= c->nspans[s]);
+            if (!used) continue;
+            for (int z : zodd)
+                if (c->ghost_h[s][n][z] != 0.0) return false;
+        }
+    return true;
+}
+
+static bool use_planar(mxe_ctx* c) {
+    if (c->tubes || c->nf != 14) return false;
+    if (c->state_planar && !bc_planar(c)) c->state_planar = false;   // stays off until set_state
+    return c->state_planar;
+}
+
+static ParamsT<float> fparams(const mxe_ctx* c) { return make_params<float>(c->sp, c->rp); }
+
+static void launch_resync(mxe_ctx* c, bool planar) {
+    dim3 rg((c->g.nx + 255) / 256, c->g.ny);
+    if (planar) mxe_resync14_2d_planar<<<rg, 256, 0, c->stream>>>(c->U, c->W, c->g);
+    else mxe_resync14_2d<<<rg, 256, 0, c->stream>>>(c->U, c->W, c->g);
+    c->w_planar = planar;
+}
+
 // ---------------------------------------------------------------- clocks
 static mxe_status reset_clock(mxe_ctx* c) {
     if (c->tubes) {
@@ -369,11 +422,19 @@ static mxe_status reset_clock(mxe_ctx* c) {
     c->launched = 0;
     int nt = 256;
     dim3 grid((c->g.nx + nt - 1) / nt, c->g.ny);
+    bool pl = use_planar(c);
     if (c->mixed) {
-        mxe_resync14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->W, c->g);
-        mxe_rate14_2d_mixed<<<grid, nt, 0, c->stream>>>(c->W, c->g, c->sp, c->clk, 0);
+        launch_resync(c, pl);
+        if (pl)
+            mxe_rate14_2d_mixed_planar<<<grid, nt, 0, c->stream>>>(c->W, c->g, fparams(c),
+                                                                   (float)c->g.idx, (float)c->g.idy,
+                                                                   c->clk, 0);
+        else
+            mxe_rate14_2d_mixed<<<grid, nt, 0, c->stream>>>(c->W, c->g, fparams(c), (float)c->g.idx,
+                                                            (float)c->g.idy, c->clk, 0);
     } else {
-        mxe_rate14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
+        if (pl) mxe_rate14_2d_planar<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
+        else mxe_rate14_2d<<<grid, nt, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, 0);
     }
     CK(cudaGetLastError());
     return MXE_OK;
@@ -391,15 +452,17 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
         CK(cudaMemcpyAsync(c->stage, soa, bytes, cudaMemcpyHostToDevice, c->stream));
         src = c->stage;
     }
-    unsigned long long init = ~0ull;
-    CK(cudaMemcpyAsync(c->scratch, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    unsigned long long init[2] = {~0ull, 0ull};
+    CK(cudaMemcpyAsync(c->scratch, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
     CellMap m = cellmap(c);
     dim3 grid = cellgrid(c, 128);
-    mxe_k_validate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->scratch);
+    mxe_k_validate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->scratch,
+                                                (unsigned*)(c->scratch + 1));
     CK(cudaGetLastError());
-    unsigned long long bad = 0;
-    CK(cudaMemcpyAsync(&bad, c->scratch, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    unsigned long long res[2] = {0, 0};
+    CK(cudaMemcpyAsync(res, c->scratch, sizeof res, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    unsigned long long bad = res[0];
     if (bad != ~0ull) {
         unsigned long long idx = bad >> 2;
         int code = (int)(bad & 3);
@@ -411,6 +474,8 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
     }
     mxe_k_setstate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->U);
     CK(cudaGetLastError());
+    c->state_planar = (res[1] == 0ull);
+    if (!c->tubes && c->Us) CK(cudaMemsetAsync(c->Us, 0, sizeof(double) * c->nelem, c->stream));
     mxe_status s = reset_clock(c);
     if (s != MXE_OK) return s;
     c->have_state = true;
@@ -551,39 +616,45 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed) {
     a.dt_fixed = dt_fixed;
     a.slot = c->slot;
     a.clk = c->clk;
+    a.idxf = (float)c->g.idx;
+    a.idyf = (float)c->g.idy;
     dim3 grid((c->g.nx + tile_x() - 1) / tile_x(), (c->g.ny + tile_y() - 1) / tile_y());
+    const bool pl = use_planar(c);
     if (c->mixed) {
-        size_t sm = stage14_2d_mixed_smem();
+        if (c->w_planar != pl) launch_resync(c, pl);       // W layout follows the kernel
+        auto kern = pl ? mxe_stage14_2d_mixed_planar : mxe_stage14_2d_mixed;
+        size_t sm = stage14_2d_mixed_smem(pl);
+        ParamsT<float> fp = fparams(c);
         a.Ubase = c->U;
         a.Uout = c->U;
         if (c->cfg.integrator == MXE_RK2) {
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
-            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
             a.Win = c->Ws; a.Wout = c->W; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
         } else {
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            mxe_stage14_2d_mixed<<<grid, 256, sm, c->stream>>>(a, c->mp);
+            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
             std::swap(c->W, c->Ws);
         }
         CK(cudaGetLastError());
         c->slot = (c->slot + 1) % 3;
         if (++c->launched % c->resync_every == 0) {
-            dim3 rg((c->g.nx + 255) / 256, c->g.ny);
-            mxe_resync14_2d<<<rg, 256, 0, c->stream>>>(c->U, c->W, c->g);
+            launch_resync(c, pl);
             CK(cudaGetLastError());
         }
         return MXE_OK;
     }
-    size_t smem = stage14_2d_f64_smem();
+    auto kern = pl ? mxe_stage14_2d_f64_planar : mxe_stage14_2d_f64;
+    size_t smem = stage14_2d_f64_smem(pl);
     if (c->cfg.integrator == MXE_RK2) {
         a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 0.5; a.final_stage = 0;
-        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+        kern<<<grid, 256, smem, c->stream>>>(a);
         a.Uin = c->Us; a.Ubase = c->U; a.Uout = c->U; a.coef = 1.0; a.final_stage = 1;
-        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+        kern<<<grid, 256, smem, c->stream>>>(a);
     } else {
         a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 1.0; a.final_stage = 1;
-        mxe_stage14_2d_f64<<<grid, 256, smem, c->stream>>>(a);
+        kern<<<grid, 256, smem, c->stream>>>(a);
         std::swap(c->U, c->Us);
     }
     CK(cudaGetLastError());
@@ -796,6 +867,7 @@ extern "C" mxe_status mxe_get_diagnostics(mxe_ctx* c, mxe_diag* out) {
         memcpy(&out->max_rate, &h.rate[c->slot], sizeof(double));
         out->n_fp64_closures = (long long)h.n_face64;
         out->n_closures = (long long)h.n_face;
+        out->planar = use_planar(c) ? 1 : 0;
     }
     return MXE_OK;
 }

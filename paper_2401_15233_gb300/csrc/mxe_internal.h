@@ -54,6 +54,7 @@ struct Stage2DArgs {
     SchemeParams sp;
     RelaxParams rp;
     double cfl, t_end, coef, dt_fixed;
+    float idxf, idyf;               // 1/dx, 1/dy for the FP32 path
     int slot, final_stage;
     DevClock* clk;
 };

@@ -505,33 +505,42 @@ __device__ __forceinline__ void flux14(const T* Q, const T* U, const T* Qk, cons
 
 // Conserved state, k-flux and wave speeds of one face state.
 template <class T, int K>
-__device__ __forceinline__ void face_eval14(const T* Q, const SchemeParams& sp, T* U, T* F,
+__device__ __forceinline__ void face_eval14(const T* Q, T sigma_lim, T k_ws, T* U, T* F,
                                             T& lmin, T& lmax) {
     Dimless14<T> d;
     dimless14(Q, d);
-    T sb = clamp_sigma(d.sig, T(sp.sigma_lim));
+    T sb = clamp_sigma(d.sig, sigma_lim);
     T Qk[6], Rk[3], Sk;
     closure14_slice<T, K>(Q, d, sb, Qk, Rk, Sk);
     prim2cons14(Q, U);
     flux14<T, K>(Q, U, Qk, Rk, Sk, F);
     T lp, lm;
     lam14_star<T, K>(d, sb, lp, lm);
-    T k = T(sp.k_ws);
-    lmax = Q[1 + K] + k * lp * d.sq;
-    lmin = Q[1 + K] + k * lm * d.sq;
+    lmax = Q[1 + K] + k_ws * lp * d.sq;
+    lmin = Q[1 + K] + k_ws * lm * d.sq;
+}
+
+template <class T, int K>
+__device__ __forceinline__ void face_eval14(const T* Q, const SchemeParams& sp, T* U, T* F,
+                                            T& lmin, T& lmax) {
+    face_eval14<T, K>(Q, T(sp.sigma_lim), T(sp.k_ws), U, F, lmin, lmax);
 }
 
 // CFL contribution max(|lmin|,|lmax|) along K and the raw sigma.
 template <class T, int K>
-__device__ __forceinline__ T amax14(const T* Q, const Dimless14<T>& d, const SchemeParams& sp) {
-    T sb = clamp_sigma(d.sig, T(sp.sigma_lim));
+__device__ __forceinline__ T amax14(const T* Q, const Dimless14<T>& d, T sigma_lim, T k_ws) {
+    T sb = clamp_sigma(d.sig, sigma_lim);
     T lp, lm;
     lam14_star<T, K>(d, sb, lp, lm);
-    T k = T(sp.k_ws);
-    T lmax = Q[1 + K] + k * lp * d.sq;
-    T lmin = Q[1 + K] + k * lm * d.sq;
+    T lmax = Q[1 + K] + k_ws * lp * d.sq;
+    T lmin = Q[1 + K] + k_ws * lm * d.sq;
     T a = fabs(lmin), b = fabs(lmax);
     return a > b ? a : b;
+}
+
+template <class T, int K>
+__device__ __forceinline__ T amax14(const T* Q, const Dimless14<T>& d, const SchemeParams& sp) {
+    return amax14<T, K>(Q, d, T(sp.sigma_lim), T(sp.k_ws));
 }
 
 // Primitive moments of cons(W) + dU from the increment alone (FP32 path):

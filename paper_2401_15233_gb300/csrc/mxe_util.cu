@@ -68,7 +68,7 @@ __device__ __forceinline__ void to_cons(const double* Q, double* U, int nf) {
 // Validate a dense input array; the smallest failing cell number and its
 // code go to bad[0], bad[1] (64-bit: code in the top bits).
 extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
-                                          unsigned long long* bad) {
+                                          unsigned long long* bad, unsigned* nonplanar) {
     long long dense, dfs, dev, fs, idx;
     if (!cell_of(m, dense, dfs, dev, fs, idx)) return;
     double V[14], Q[14];
@@ -77,6 +77,10 @@ extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const dou
     else to_prim(V, Q, nf);
     int code = check_prim(Q, nf);
     if (code) atomicMin(bad, ((unsigned long long)idx << 2) | (unsigned long long)code);
+    // planar iff the z-odd moments (u_z, P_xz, P_yz, q_z) vanish; on the
+    // conserved side they are rho u_z, E_xz, E_yz, H_z (same positions)
+    if (nf == 14 && (V[3] != 0.0 || V[6] != 0.0 || V[8] != 0.0 || V[12] != 0.0))
+        atomicOr(nonplanar, 1u);
 }
 
 extern "C" __global__ void mxe_k_setstate(CellMap m, int nf, int kind, const double* src,

@@ -178,7 +178,14 @@ def smooth_field14(rng, nx: int, ny: int, amp: float = 0.3, planar: bool = True)
     # kurtosis a little above Gaussian so sigma stays well inside (0, 1)
     R = (1.0 + 0.05 * amp * f(0) * f(3)) * 15.0 * P * P / rho
     Z = np.zeros_like(X)
-    st = np.stack([rho, ux, uy, Z, Pxx, Pxy, Z, Pyy, Z, Pzz, qx, qy, Z, R], axis=-1)
+    if planar:
+        uz, Pxz, Pyz, qz = Z, Z, Z, Z
+    else:     # z-odd moments switched on (small, keeping P positive definite)
+        uz = 0.5 * amp * f(5) * f(1)
+        Pxz = 0.04 * amp * P * f(2)
+        Pyz = 0.03 * amp * P * f(6)
+        qz = 0.05 * amp * rho * th ** 1.5 * f(4)
+    st = np.stack([rho, ux, uy, uz, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz, qx, qy, qz, R], axis=-1)
     return st
 
 
@@ -199,7 +206,8 @@ def maxwellian_mixture14(comps):
     return np.array([rho, *u, P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2], *q, R])
 
 
-def jets_like_field(nx: int, ny: int, setup: dict, spread=0.35, reach=0.8, rng=None):
+def jets_like_field(nx: int, ny: int, setup: dict, spread=0.35, reach=0.8, rng=None,
+                    uz_beam: float = 0.0):
     """A synthetic, developed-looking crossed-jets state on [0,1]^2: background
     gas plus two Maxwellian beams (the inflow states) whose densities decay
     away from the slots and spread with distance, so that the crossing
@@ -226,24 +234,30 @@ def jets_like_field(nx: int, ny: int, setup: dict, spread=0.35, reach=0.8, rng=N
     w1 = rj * beam(X, Y - yc)
     w2 = rj * beam(Y, X - yc)
     # vectorised mixture of three Maxwellians
-    comps = [(np.full_like(X, rb), (0.0, 0.0), Tb), (w1 + 1e-30, (ux, 0.0), Tj),
-             (w2 + 1e-30, (0.0, uy), Tj)]
+    comps = [(np.full_like(X, rb), (0.0, 0.0, 0.0), Tb), (w1 + 1e-30, (ux, 0.0, uz_beam), Tj),
+             (w2 + 1e-30, (0.0, uy, 0.0), Tj)]
     rho = sum(c[0] for c in comps)
-    u = [sum(c[0] * c[1][d] for c in comps) / rho for d in range(2)]
+    u = [sum(c[0] * c[1][d] for c in comps) / rho for d in range(3)]
     out = np.zeros((ny, nx, 14))
     out[..., 0] = rho
-    out[..., 1], out[..., 2] = u
-    Pxx = Pxy = Pyy = Pzz = q0 = q1 = R = 0.0
+    out[..., 1], out[..., 2], out[..., 3] = u
+    P = [[0.0] * 3 for _ in range(3)]
+    q = [0.0] * 3
+    R = 0.0
     for ra, ua, Ta in comps:
-        cx, cy = ua[0] - u[0], ua[1] - u[1]
-        c2 = cx * cx + cy * cy
-        Pxx = Pxx + ra * (Ta + cx * cx)
-        Pyy = Pyy + ra * (Ta + cy * cy)
-        Pzz = Pzz + ra * Ta
-        Pxy = Pxy + ra * cx * cy
-        q0 = q0 + ra * cx * (c2 + 5 * Ta)
-        q1 = q1 + ra * cy * (c2 + 5 * Ta)
+        c = [ua[d] - u[d] for d in range(3)]
+        c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2]
+        for i in range(3):
+            for j in range(3):
+                P[i][j] = P[i][j] + ra * ((Ta if i == j else 0.0) + c[i] * c[j])
+            q[i] = q[i] + ra * c[i] * (c2 + 5 * Ta)
         R = R + ra * (c2 * c2 + 10 * Ta * c2 + 15 * Ta * Ta)
-    out[..., 4], out[..., 5], out[..., 7], out[..., 9] = Pxx, Pxy, Pyy, Pzz
-    out[..., 10], out[..., 11], out[..., 13] = q0, q1, R
+    out[..., 4], out[..., 5], out[..., 6] = P[0][0], P[0][1], P[0][2]
+    out[..., 7], out[..., 8], out[..., 9] = P[1][1], P[1][2], P[2][2]
+    out[..., 10], out[..., 11], out[..., 12], out[..., 13] = q[0], q[1], q[2], R
+    if uz_beam == 0.0:        # exact zeros for the z-odd moments of a planar state
+        out[..., 3] = 0.0
+        out[..., 6] = 0.0
+        out[..., 8] = 0.0
+        out[..., 12] = 0.0
     return out

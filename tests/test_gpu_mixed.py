@@ -44,8 +44,9 @@ POLICIES = {"off": (0.0, 2.0, 0.0), "default": (0.0, 0.999, 1e-3),
             "wide": (1e-2, 0.99, 1e-2), "all": (0.0, 0.0, 2.0)}
 
 
+@pytest.mark.parametrize("planar", [True, False])
 @pytest.mark.parametrize("policy", list(POLICIES))
-def test_mixed_per_step_error_by_policy(mx, orc, policy):
+def test_mixed_per_step_error_by_policy(mx, orc, policy, planar):
     """One mixed step from the oracle's state, for each FP64-closure policy:
     the error (FP32 arithmetic through the whole stage) is reported next to
     the step's sensitivity to a 1e-7 data perturbation, and bounded by 1e-4
@@ -53,7 +54,7 @@ def test_mixed_per_step_error_by_policy(mx, orc, policy):
     n = 48
     setup = wl.jets_setup(Kn=0.1)
     rng = np.random.default_rng(11)
-    prim = wl.jets_like_field(n, n, setup)
+    prim = wl.jets_like_field(n, n, setup, uz_beam=0.0 if planar else 0.8)
     cfg = jets_oracle_cfg(orc, n, n, setup)
     s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
     s.set_mixed_policy(*POLICIES[policy], resync_every=16)
@@ -71,7 +72,8 @@ def test_mixed_per_step_error_by_policy(mx, orc, policy):
         sens_min = np.minimum(sens_min, sens)
         U = U1
     d = s.diagnostics()
-    print(f"policy {policy}: mixed per-step error max {worst.max():.2e} "
+    assert d["planar"] == int(planar)
+    print(f"policy {policy} planar={planar}: mixed per-step error max {worst.max():.2e} "
           f"(sensitivity min {sens_min[sens_min > 0].min():.2e}); "
           f"FP64 closures {d['n_fp64_closures']} of {d['n_closures']}")
     if policy == "all":
@@ -157,7 +159,8 @@ def test_mixed_sampled_4096_bench_config(mx, orc):
     s.set_state(aos_to_soa(Ufull), kind="conserved")
     cfg = jets_oracle_cfg(orc, n, n, setup)
     sub = Ufull[::64, ::64]
-    rms = np.sqrt((sub.reshape(-1, 14) ** 2).mean(axis=0))
+    from tests.test_gpu_parity import family_scale
+    rms = family_scale(np.sqrt((sub.reshape(-1, 14) ** 2).mean(axis=0)))
     dt = 2.5e-8
     s.step_dt([dt])
     G = s.get_moments("conserved")
