@@ -222,19 +222,44 @@ __device__ __forceinline__ double step_dt_m(const DevClock* clk, int slot, doubl
     return dt;
 }
 
+// Own-cell prefetch of the final stage (U^n FP64 and W^n FP32 into shared
+// memory at kernel start): on for the ten-field planar state, where it
+// still fits two blocks per SM.
+template <int NF>
+constexpr int prefetch_cells() { return NF == NP ? TXm * TYm : 0; }
+
+// shared memory: own-cell prefetch, stencil box, x and y face fluxes,
+// staged left face states, limiters, reduction scratch
 template <int NF>
 constexpr size_t smem_mixed() {
-    return sizeof(float) * (NF * NBOXm + NF * NTm + (2 * NF + 2) * NTm + NPHXm + NPHYm + 8);
+    return sizeof(double) * (NF * prefetch_cells<NF>()) +
+           sizeof(float) * (NF * prefetch_cells<NF>() + NF * NBOXm + 2 * NF * NTm +
+                            (2 * NF + 2) * NTm + NPHXm + NPHYm + 8);
 }
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}
+
 
 template <class PH>
 __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<float>& p,
                                             const MixedPolicy& mp) {
     constexpr int NF = PH::NF;
-    extern __shared__ __align__(16) float smf[];
-    float* W = smf;                                  // [NF][BY][BX]
-    float* Fb = W + NF * NBOXm;                      // [NF][256]
-    float* Ls = Fb + NF * NTm;                       // [2NF+2][256] left face states
+    constexpr int NC = TXm * TYm;
+    constexpr int PF = prefetch_cells<NF>();
+    extern __shared__ __align__(16) double smd[];
+    double* Upf = smd;                               // [NF][PF] own-cell U^n (final stage)
+    float* Wpf = (float*)(Upf + NF * PF);            // [NF][PF] own-cell W^n (final stage)
+    float* W = Wpf + NF * PF;                        // [NF][BY][BX]
+    float* Fx = W + NF * NBOXm;                      // [NF][256] x-face fluxes
+    float* Fy = Fx + NF * NTm;                       // [NF][256] y-face fluxes
+    float* Ls = Fy + NF * NTm;                       // [2NF+2][256] left face states
     float* phx = Ls + (2 * NF + 2) * NTm;            // [TY][TX+2]
     float* phy = phx + NPHXm;                        // [TY+2][TX]
     float* red = phy + NPHYm;                        // [8]
@@ -266,6 +291,21 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
 
     const Grid2D& g = a.g;
     const int i0 = blockIdx.x * TXm, j0 = blockIdx.y * TYm;
+    const int cx = tid % TXm, cy = tid / TXm;
+    const bool owner = tid < NC;
+    const int gi = i0 + cx, gj = j0 + cy;
+    const bool inside = owner && gi < g.nx && gj < g.ny;
+    const long long o = (long long)gj * g.pitch + gi;
+    // final stage: start fetching this cell's U^n and W^n now; they are
+    // needed only after all face fluxes are done
+    if (PF && a.final_stage && inside) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            cp_async8(Upf + k * PF + tid, a.Ubase + o + PH::ufield(k) * g.fstride);
+            cp_async4(Wpf + k * PF + tid, a.Wbase + o + k * g.fstride);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
     for (int c = tid; c < NBOXm; c += NTm) {
         int bx = c % BXm, by = c / BXm;
         float Q[NF];
@@ -274,31 +314,45 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
         for (int k = 0; k < NF; ++k) W[k * NBOXm + c] = Q[k];
     }
     __syncthreads();
-    for (int n = tid; n < NPHXm; n += NTm) {
-        int bx = 1 + n % (TXm + 2), by = 2 + n / (TXm + 2);
-        phx[n] = p.order == 2 ? phi_box_m<NF>(W, by * BXm + bx, 1, p.limiter) : 0.0f;
-    }
-    for (int n = tid; n < NPHYm; n += NTm) {
-        int bx = 2 + n % TXm, by = 1 + n / TXm;
-        phy[n] = p.order == 2 ? phi_box_m<NF>(W, by * BXm + bx, BXm, p.limiter) : 0.0f;
+    for (int n = tid; n < NPHXm + NPHYm; n += NTm) {
+        float v = 0.0f;
+        if (n < NPHXm) {
+            int bx = 1 + n % (TXm + 2), by = 2 + n / (TXm + 2);
+            if (p.order == 2) v = phi_box_m<NF>(W, by * BXm + bx, 1, p.limiter);
+            phx[n] = v;
+        } else {
+            int m = n - NPHXm;
+            int bx = 2 + m % TXm, by = 1 + m / TXm;
+            if (p.order == 2) v = phi_box_m<NF>(W, by * BXm + bx, BXm, p.limiter);
+            phy[m] = v;
+        }
     }
     __syncthreads();
 
     const double sl64 = a.sp.sigma_lim, kw64 = a.sp.k_ws;
     unsigned nflag = 0;
-    {
-        int fx = tid & 15, cy = tid >> 4, by = cy + 2;
+    {   // x face tid, then y face tid (no barrier in between)
+        int fx = tid & 15, fcy = tid >> 4, by = fcy + 2;
         float F[NF];
-        face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1, phx[cy * (TXm + 2) + fx],
-                           phx[cy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, Ls + tid, F, nflag);
+        face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1, phx[fcy * (TXm + 2) + fx],
+                           phx[fcy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, Ls + tid, F, nflag);
 #pragma unroll
-        for (int k = 0; k < NF; ++k) Fb[k * NTm + tid] = F[k];
+        for (int k = 0; k < NF; ++k) Fx[k * NTm + tid] = F[k];
+        if (tid < TXm * (TYm + 1)) {
+            int fcx = tid % TXm, fy = tid / TXm, bx = fcx + 2;
+            face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm,
+                               phy[fy * TXm + fcx], phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64,
+                               Ls + tid, F, nflag);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) Fy[k * NTm + tid] = F[k];
+        }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
-    const int cx = tid % TXm, cy = tid / TXm;
-    const bool owner = tid < TXm * TYm;
-    float L[NF];
+
+    float r = 0.0f;
     if (owner) {
+        float L[NF];
         float Qc[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) Qc[k] = W[k * NBOXm + (cy + 2) * BXm + cx + 2];
@@ -309,28 +363,11 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
             for (int k = 0; k < NF; ++k) L[k] = 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < NF; ++k)
-            L[k] -= (Fb[k * NTm + cy * 16 + cx + 1] - Fb[k * NTm + cy * 16 + cx]) * a.idxf;
-    }
-    __syncthreads();
-    if (tid < TXm * (TYm + 1)) {
-        int fcx = tid % TXm, fy = tid / TXm, bx = fcx + 2;
-        float F[NF];
-        face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm, phy[fy * TXm + fcx],
-                           phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64, Ls + tid, F, nflag);
-#pragma unroll
-        for (int k = 0; k < NF; ++k) Fb[k * NTm + tid] = F[k];
-    }
-    __syncthreads();
-
-    float r = 0.0f;
-    if (owner) {
-#pragma unroll
-        for (int k = 0; k < NF; ++k)
-            L[k] -= (Fb[k * NTm + (cy + 1) * TXm + cx] - Fb[k * NTm + cy * TXm + cx]) * a.idyf;
-        int gi = i0 + cx, gj = j0 + cy;
-        if (gi < g.nx && gj < g.ny) {
-            long long o = (long long)gj * g.pitch + gi;
+        for (int k = 0; k < NF; ++k) {
+            L[k] -= (Fx[k * NTm + cy * 16 + cx + 1] - Fx[k * NTm + cy * 16 + cx]) * a.idxf;
+            L[k] -= (Fy[k * NTm + (cy + 1) * TXm + cx] - Fy[k * NTm + cy * TXm + cx]) * a.idyf;
+        }
+        if (inside) {
             float cdt = (float)(a.coef * dt);
             float dU[NF], Wc[NF], Wn[NF];
 #pragma unroll
@@ -346,11 +383,11 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
                 bool bad = false;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
-                    long long ok = o + PH::ufield(k) * g.fstride;
-                    double un = a.Ubase[ok] + (double)dU[k];
-                    a.Uout[ok] = un;
+                    double ub = PF ? Upf[k * PF + tid] : a.Ubase[o + PH::ufield(k) * g.fstride];
+                    double un = ub + (double)dU[k];
+                    a.Uout[o + PH::ufield(k) * g.fstride] = un;
                     bad |= !isfinite(un);
-                    Wc[k] = a.Wbase[o + k * g.fstride];
+                    Wc[k] = PF ? Wpf[k * PF + tid] : a.Wbase[o + k * g.fstride];
                 }
                 PH::increment(Wc, dU, Wn);
 #pragma unroll

@@ -83,6 +83,27 @@ __device__ __forceinline__ T hyp_bracket(T zeta, T D0) {
     return zeta >= T(0) ? zeta + rt : D0 / (rt - zeta);
 }
 
+// B = 5 - 4 sqrt(s) + sqrt(10 - 16 sqrt(s) + 6 s) and Y = B + E^2 - 2 E sqrt(B)
+// of the wave-speed fits.  Double: as printed.  Float: the algebraically
+// identical 10 - 16 r + 6 r^2 = 2 (5 - 3 r)(1 - r) (r = sqrt s) and
+// Y = (sqrt B - E)^2, which keep their digits as sigma -> 1.
+template <class T> struct WsTerms;
+template <> struct WsTerms<double> {
+    static __device__ __forceinline__ void get(double ssb, double sb, double E, double& B,
+                                               double& Y) {
+        B = 5.0 - 4.0 * ssb + ::sqrt(10.0 - 16.0 * ssb + 6.0 * sb);
+        Y = B + E * E - 2.0 * E * ::sqrt(B);
+    }
+};
+template <> struct WsTerms<float> {
+    static __device__ __forceinline__ void get(float ssb, float sb, float E, float& B,
+                                               float& Y) {
+        B = 5.0f - 4.0f * ssb + ::sqrtf(2.0f * (5.0f - 3.0f * ssb) * (1.0f - ssb));
+        float d = ::sqrtf(B) - E;
+        Y = d * d;
+    }
+};
+
 // =========================================================================
 // 5-moment system (Sec. 2.3)
 // =========================================================================
@@ -127,6 +148,29 @@ __device__ __forceinline__ T lam5_star(T qs, T sb, T E, T C, T Y) {
     return hyp_bracket(qs, D0) / (T(2) * sb) + E;
 }
 
+// Primitive moments of cons5(W) + dU from the increment alone (FP32 path;
+// every term scales with the increment, see prim_increment14).
+__device__ __forceinline__ void prim_increment5(const float* W, const float* dU, float* Wn) {
+    float rho = W[0], u = W[1], P = W[2], q = W[3];
+    float drho = dU[0];
+    float rho1 = rho + drho;
+    float du = (dU[1] - u * drho) / rho1;
+    float u1 = u + du;
+    float dP = dU[2] - drho * u * u - rho1 * (2.0f * u * du + du * du);
+    float P1 = P + dP;
+    float s = 2.0f * u * du + du * du;                      // u1^2 - u^2
+    // G = rho u^3 + 3 u P
+    float dG = drho * u * u * u + rho1 * du * (3.0f * u * u + 3.0f * u * du + du * du)
+             + 3.0f * (du * P1 + u * dP);
+    float dq = dU[3] - dG;
+    float q1 = q + dq;
+    // K = rho u^4 + 6 u^2 P + 4 u q
+    float dK = drho * u * u * u * u + rho1 * s * (2.0f * u * u + s) + 6.0f * (s * P1 + u * u * dP)
+             + 4.0f * (du * q1 + u * dq);
+    Wn[0] = rho1; Wn[1] = u1; Wn[2] = P1; Wn[3] = q1;
+    Wn[4] = W[4] + (dU[4] - dK);
+}
+
 // Raw sigma of Eq. (sigma-mapping-5mom) from the dimensionless q*, r*.
 template <class T>
 __device__ __forceinline__ T sigma5(T qs, T rs) {
@@ -135,6 +179,33 @@ __device__ __forceinline__ T sigma5(T qs, T rs) {
 
 // Face-state evaluation: conserved U, x-flux F (Eq. 5mom-sys-eqs with the
 // closure of Eq. closure-1D1V-s-approx) and wave speeds.
+template <class T>
+__device__ __forceinline__ void face_eval5(const T* Q, T sigma_lim, T k_ws, T* U, T* F,
+                                           T& lmin, T& lmax) {
+    T rho = Q[0], u = Q[1], P = Q[2], q = Q[3], r = Q[4];
+    T th = P / rho;
+    T sq = M<T>::sqrt_(th);
+    T sc3 = rho * th * sq;
+    T qs = q / sc3;
+    T rs = r / (rho * th * th);
+    T sb = clamp_sigma(sigma5(qs, rs), sigma_lim);
+    T ssb = M<T>::sqrt_(sb);
+    T ss = qs * qs * qs / (sb * sb) + (T(10) - T(8) * ssb) * qs;
+    T s = ss * sc3 * th;
+    prim2cons5(Q, U);
+    F[0] = rho * u;
+    F[1] = rho * u * u + P;
+    F[2] = rho * u * u * u + T(3) * u * P + q;
+    F[3] = rho * u * u * u * u + T(6) * u * u * P + T(4) * u * q + r;
+    F[4] = rho * u * u * u * u * u + T(10) * u * u * u * P + T(10) * u * u * q + T(5) * u * r + s;
+    T C = M<T>::sqrt_(T(3) - T(3) * sb);
+    T E = T(0.8) * C;
+    T B, Y;
+    WsTerms<T>::get(ssb, sb, E, B, Y);
+    lmax = u + k_ws * lam5_star(qs, sb, E, C, Y) * sq;
+    lmin = u - k_ws * lam5_star(-qs, sb, E, C, Y) * sq;
+}
+
 template <class T>
 __device__ __forceinline__ void face_eval5(const T* Q, const SchemeParams& sp, T* U, T* F,
                                            T& lmin, T& lmax) {
@@ -364,27 +435,6 @@ __device__ __forceinline__ void dimless14(const T* Q, Dimless14<T>& d) {
     T X = T(8) * d.T2 * qPq;
     d.sig = sigma_root(A, X, d.T2);
 }
-
-// B = 5 - 4 sqrt(s) + sqrt(10 - 16 sqrt(s) + 6 s) and Y = B + E^2 - 2 E sqrt(B)
-// of the wave-speed fits.  Double: as printed.  Float: the algebraically
-// identical 10 - 16 r + 6 r^2 = 2 (5 - 3 r)(1 - r) (r = sqrt s) and
-// Y = (sqrt B - E)^2, which keep their digits as sigma -> 1.
-template <class T> struct WsTerms;
-template <> struct WsTerms<double> {
-    static __device__ __forceinline__ void get(double ssb, double sb, double E, double& B,
-                                               double& Y) {
-        B = 5.0 - 4.0 * ssb + ::sqrt(10.0 - 16.0 * ssb + 6.0 * sb);
-        Y = B + E * E - 2.0 * E * ::sqrt(B);
-    }
-};
-template <> struct WsTerms<float> {
-    static __device__ __forceinline__ void get(float ssb, float sb, float E, float& B,
-                                               float& Y) {
-        B = 5.0f - 4.0f * ssb + ::sqrtf(2.0f * (5.0f - 3.0f * ssb) * (1.0f - ssb));
-        float d = ::sqrtf(B) - E;
-        Y = d * d;
-    }
-};
 
 // Eq. (14mom-approx-ws-equations): lambda*_max and lambda*_min along k.
 template <class T, int K>
