@@ -181,10 +181,16 @@ const char *mxe_last_error(const mxe_ctx *ctx);
 
 /* Create n independent 1D problems (cfg->ny must be 1; cfg->nx is ignored):
  * tube b has ncells[b] cells on [0, length[b]].  All tubes share system,
- * precision, scheme and CFL; each has its own state, BCs (transmissive by
- * default), relaxation time and clock.  mxe_set_state / mxe_get_moments act
- * on the concatenation of all tubes.  The whole batch advances in one
- * persistent launch (one thread block or cluster per tube). */
+ * precision, scheme, CFL and boundary conditions (transmissive by default);
+ * each has its own state, relaxation time and clock.  mxe_set_state /
+ * mxe_get_moments act on the concatenation of all tubes.  The whole batch
+ * advances in one persistent launch.  MXE_FP64: one thread block per tube.
+ * MXE_MIXED (14-moment system): teams of CTAs (thread-block clusters of
+ * 1, 2, 4 or 8 CTAs of 128 or 256 threads, see mxe_batch_autotune) take
+ * tubes from a device work queue, longest expected work (cells / dx) first;
+ * each mxe_batch_run / mxe_step replays a cached CUDA graph of that launch.
+ * Errors: MXE_EINVAL for a bad tube list (n < 1, ncells[b] < 4, length[b]
+ * <= 0), MXE_ENOMEM / MXE_ECUDA when device allocation fails. */
 mxe_status mxe_batch_create(const mxe_config *cfg, int n, const int *ncells,
                             const double *length, mxe_ctx **out);
 
@@ -198,6 +204,22 @@ mxe_status mxe_batch_get_clock(mxe_ctx *ctx, double *t, long long *steps);
 /* Advance every tube until its own t reaches t_end or it has taken
  * max_steps steps in this call; one launch for the whole batch. */
 mxe_status mxe_batch_run(mxe_ctx *ctx, int max_steps, double t_end);
+
+/* MXE_MIXED tube contexts: time every block shape (128 or 256 threads per
+ * CTA x teams of 1, 2, 4 or 8 CTAs) on the current state advanced by t_probe
+ * (each candidate from the same saved state and clocks, which are restored
+ * afterwards) and keep the fastest for later runs.  Shapes that cannot be
+ * resident on the device are skipped.  Outputs (may be NULL): the chosen
+ * threads per CTA, CTAs per team and its time in ms.  Allocates (and frees)
+ * one temporary copy of the state; synchronises the context stream.
+ * Errors: MXE_ESTATE (not an MXE_MIXED 1D context, or no state),
+ * MXE_EINVAL (t_probe <= 0), MXE_ECUDA. */
+mxe_status mxe_batch_autotune(mxe_ctx *ctx, double t_probe, int *nt_out, int *cl_out,
+                              double *ms_out);
+
+/* MXE_MIXED tube contexts: set the block shape directly (nt in {128, 256},
+ * cl in {1, 2, 4, 8}); the default is 128 x 1. */
+mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
 
 /* ---- fixed-scratch 1D solve (allocates nothing) -------------------------- */
 

@@ -24,6 +24,7 @@ __all__ = [
     "mxe_get_moments", "mxe_set_bc", "mxe_set_relaxation", "mxe_step", "mxe_step_dt",
     "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
     "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy", "mxe_tube_run_noalloc",
+    "mxe_batch_autotune", "mxe_batch_set_shape",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
@@ -102,6 +103,9 @@ def lib():
                                           C.c_double], C.c_int),
             "mxe_batch_get_clock": ([_P, _P, _P], C.c_int),
             "mxe_batch_run": ([_P, C.c_int, C.c_double], C.c_int),
+            "mxe_batch_autotune": ([_P, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double)], C.c_int),
+            "mxe_batch_set_shape": ([_P, C.c_int, C.c_int], C.c_int),
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
             "mxe_tube_run_noalloc": ([C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_double, _P, C.c_double, C.c_double,
@@ -250,6 +254,16 @@ def mxe_batch_run(ctx, max_steps, t_end):
     _check(ctx, lib().mxe_batch_run(ctx, max_steps, t_end))
 
 
+def mxe_batch_autotune(ctx, t_probe):
+    nt, cl, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    _check(ctx, lib().mxe_batch_autotune(ctx, t_probe, C.byref(nt), C.byref(cl), C.byref(ms)))
+    return nt.value, cl.value, ms.value
+
+
+def mxe_batch_set_shape(ctx, nt, cl):
+    _check(ctx, lib().mxe_batch_set_shape(ctx, nt, cl))
+
+
 # ------------------------------------------------------------ convenience
 _ENUM = {
     "fp64": FP64, "mixed": MIXED, "hll": FLUX_HLL, "rusanov": FLUX_RUSANOV,
@@ -360,3 +374,11 @@ class Batch(Solver):
 
     def run(self, max_steps, t_end):
         mxe_batch_run(self.ctx, max_steps, t_end)
+
+    def autotune(self, t_probe):
+        """Time every block shape over t_probe (state restored); returns
+        (threads per CTA, CTAs per team, ms of the fastest)."""
+        return mxe_batch_autotune(self.ctx, t_probe)
+
+    def set_shape(self, nt, cl):
+        mxe_batch_set_shape(self.ctx, nt, cl)

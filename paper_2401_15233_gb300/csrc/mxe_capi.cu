@@ -17,7 +17,7 @@
 #include "../../include/maxent.h"
 #include "mxe_internal.h"
 
-#include "mxe_policy.cuh"
+#include "mxe_mixed.cuh"
 
 namespace mxe {
 // kernels defined in the other translation units
@@ -30,9 +30,6 @@ extern "C" __global__ void mxe_rate14_2d_planar(const double* U, Grid2D g, Schem
 extern "C" __global__ void mxe_tubes5_f64(const TubeArgs a);
 extern "C" __global__ void mxe_tubes14_f64(const TubeArgs a);
 size_t stage14_2d_f64_smem(bool planar);
-struct MixedPolicy {
-    float sig_lo, sig_hi, det_min;
-};
 extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const ParamsT<float> p,
                                                 const MixedPolicy mp);
 extern "C" __global__ void mxe_stage14_2d_mixed_planar(const Stage2DArgs a,
@@ -46,6 +43,8 @@ extern "C" __global__ void mxe_rate14_2d_mixed_planar(const float* W, Grid2D g,
                                                       ParamsT<float> p, float idxf, float idyf,
                                                       DevClock* clk, int slot);
 size_t stage14_2d_mixed_smem(bool planar);
+const void* tubes_mixed_kernel(bool planar, int nt);
+size_t tubes_mixed_smem(bool planar, int nt);
 int tile_x();
 int tile_y();
 int tubes_threads();
@@ -79,6 +78,17 @@ struct mxe_ctx {
     std::vector<int> tn;
     TubeDesc* tdesc_d = nullptr;
     TubeClock* tclk = nullptr;
+    int* order_d = nullptr;           // mixed tubes: hand-out order (longest work first)
+    int* queue_d = nullptr;           // mixed tubes: work counter
+    int tune_nt = 128, tune_cl = 1;   // block shape of the mixed tube launch
+    bool tuned = false;
+    int nsm = 0;
+    cudaStream_t cap_stream = nullptr;     // graph capture only (never executes work)
+    cudaGraphExec_t gexec = nullptr;       // captured [queue reset, persistent launch]
+    double g_tend = -1.0;
+    int g_steps = -1, g_nt = 0, g_cl = 0;
+    long long g_gen = -1;
+    long long gen = 0;                // bumped whenever launch arguments change
     // state
     double* U = nullptr;
     double* Us = nullptr;
@@ -169,8 +179,8 @@ static mxe_status check_cfg(mxe_ctx* c, const mxe_config* cfg, bool batch) {
         return fail(c, MXE_EINVAL, "the 5-moment (1D1V) system needs ny == 1");
     if (cfg->precision != MXE_FP64 && cfg->precision != MXE_MIXED)
         return fail(c, MXE_EINVAL, "precision must be MXE_FP64 or MXE_MIXED");
-    if (cfg->precision == MXE_MIXED && (batch || cfg->ny == 1 || cfg->system != 14))
-        return fail(c, MXE_EINVAL, "MXE_MIXED is available for 2D 14-moment grids");
+    if (cfg->precision == MXE_MIXED && cfg->system != 14)
+        return fail(c, MXE_EINVAL, "MXE_MIXED is available for the 14-moment system");
     if (cfg->flux != MXE_FLUX_HLL && cfg->flux != MXE_FLUX_RUSANOV)
         return fail(c, MXE_EINVAL, "unknown flux %d", cfg->flux);
     if (cfg->limiter != MXE_LIM_MINMOD && cfg->limiter != MXE_LIM_VANALBADA)
@@ -214,6 +224,38 @@ static mxe_status alloc_common(mxe_ctx* c) {
     return MXE_OK;
 }
 
+// Tube contexts: device descriptors and clocks; for the mixed path also the
+// work queue, its hand-out order (largest n/dx first: a tube's work grows as
+// cells x steps ~ n^2 / length), the capture stream and the kernel
+// attributes of every block shape.
+static mxe_status tubes_setup(mxe_ctx* c) {
+    const int n = c->ntubes;
+    CK(cudaMalloc(&c->tdesc_d, sizeof(TubeDesc) * n));
+    CK(cudaMalloc(&c->tclk, sizeof(TubeClock) * n));
+    CK(cudaMemset(c->tclk, 0, sizeof(TubeClock) * n));
+    CK(cudaMemcpy(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * n, cudaMemcpyHostToDevice));
+    if (!c->mixed) return MXE_OK;
+    std::vector<int> order(n);
+    for (int b = 0; b < n; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return c->tdesc[x].n / c->tdesc[x].dx > c->tdesc[y].n / c->tdesc[y].dx;
+    });
+    CK(cudaMalloc(&c->order_d, sizeof(int) * n));
+    CK(cudaMemcpy(c->order_d, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->queue_d, sizeof(int)));
+    CK(cudaMemset(c->queue_d, 0, sizeof(int)));
+    CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (int pl = 0; pl < 2; ++pl)
+        for (int nt = 128; nt <= 256; nt *= 2)
+            CK(cudaFuncSetAttribute(tubes_mixed_kernel(pl, nt),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tubes_mixed_smem(pl, nt)));
+    return MXE_OK;
+}
+
 extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     if (!out) return MXE_EINVAL;
     *out = nullptr;
@@ -253,13 +295,7 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     }
     s = alloc_common(c);
     if (s == MXE_OK && c->tubes) {
-        cudaError_t e = cudaMalloc(&c->tdesc_d, sizeof(TubeDesc) * c->ntubes);
-        if (e == cudaSuccess) e = cudaMalloc(&c->tclk, sizeof(TubeClock) * c->ntubes);
-        if (e == cudaSuccess) e = cudaMemset(c->tclk, 0, sizeof(TubeClock) * c->ntubes);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * c->ntubes,
-                           cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) s = fail(c, MXE_ECUDA, "tube set-up: %s", cudaGetErrorString(e));
+        s = tubes_setup(c);
     } else if (s == MXE_OK) {
         cudaError_t e = cudaMalloc(&c->clk, sizeof(DevClock));
         if (e == cudaSuccess) e = cudaMemset(c->clk, 0, sizeof(DevClock));
@@ -308,6 +344,7 @@ extern "C" mxe_status mxe_batch_create(const mxe_config* cfg, int n, const int* 
     }
     c->cfg = *cfg;
     c->nf = cfg->system;
+    c->mixed = cfg->precision == MXE_MIXED;
     c->tubes = true;
     c->ntubes = n;
     long long off = 0;
@@ -318,6 +355,7 @@ extern "C" mxe_status mxe_batch_create(const mxe_config* cfg, int n, const int* 
         }
         TubeDesc td{};
         td.off = off;
+        td.coff = c->ncell;
         td.n = ncells[b];
         td.dx = length[b] / ncells[b];
         td.rp = c->rp;
@@ -328,15 +366,7 @@ extern "C" mxe_status mxe_batch_create(const mxe_config* cfg, int n, const int* 
     }
     c->nelem = off;
     s = alloc_common(c);
-    if (s == MXE_OK) {
-        cudaError_t e = cudaMalloc(&c->tdesc_d, sizeof(TubeDesc) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&c->tclk, sizeof(TubeClock) * n);
-        if (e == cudaSuccess) e = cudaMemset(c->tclk, 0, sizeof(TubeClock) * n);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * n,
-                           cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) s = fail(c, MXE_ECUDA, "tube set-up: %s", cudaGetErrorString(e));
-    }
+    if (s == MXE_OK) s = tubes_setup(c);
     if (s != MXE_OK) {
         mxe_destroy(c);
         return s;
@@ -361,6 +391,10 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->tdesc_d);
     cudaFree(c->tclk);
     cudaFree(c->dts_d);
+    cudaFree(c->order_d);
+    cudaFree(c->queue_d);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -475,6 +509,7 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
     mxe_k_setstate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->U);
     CK(cudaGetLastError());
     c->state_planar = (res[1] == 0ull);
+    ++c->gen;
     if (!c->tubes && c->Us) CK(cudaMemsetAsync(c->Us, 0, sizeof(double) * c->nelem, c->stream));
     mxe_status s = reset_clock(c);
     if (s != MXE_OK) return s;
@@ -539,6 +574,7 @@ static mxe_status upload_ghosts(mxe_ctx* c) {
 extern "C" mxe_status mxe_set_bc(mxe_ctx* c, int side, int type, double lo, double hi,
                                  const double* prim) {
     if (!c) return MXE_EINVAL;
+    ++c->gen;
     int nsides = c->tubes ? 2 : 4;
     if (side < 0 || side >= nsides) return fail(c, MXE_EINVAL, "bad side %d", side);
     if (type < 0 || type > 2) return fail(c, MXE_EINVAL, "bad BC type %d", type);
@@ -573,6 +609,7 @@ extern "C" mxe_status mxe_set_relaxation(mxe_ctx* c, int model, double tau_ref, 
     if (model == 2 && !(rho_ref > 0.0 && T_ref > 0.0))
         return fail(c, MXE_EINVAL, "rho_ref and T_ref must be > 0");
     c->rp = RelaxParams{model, tau_ref, rho_ref, T_ref};
+    ++c->gen;
     if (c->tubes) {
         for (auto& td : c->tdesc) td.rp = c->rp;
         CK(cudaMemcpyAsync(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * c->ntubes,
@@ -668,8 +705,159 @@ static mxe_status read_clock_2d(mxe_ctx* c, DevClock* h) {
     return MXE_OK;
 }
 
+// ---------------------------------------------------------------- mixed tubes
+static bool tubes_planar(mxe_ctx* c) { return c->nf == 14 && c->state_planar && bc_planar(c); }
+
+static mxe_status upload_dts(mxe_ctx* c, const double* dts, int ndts) {
+    if (ndts > c->dts_cap) {
+        cudaFree(c->dts_d);
+        c->dts_d = nullptr;
+        CK(cudaMalloc(&c->dts_d, sizeof(double) * ndts));
+        c->dts_cap = ndts;
+    }
+    CK(cudaMemcpyAsync(c->dts_d, dts, sizeof(double) * ndts, cudaMemcpyHostToDevice, c->stream));
+    return MXE_OK;
+}
+
+static TubeMixedArgs tubes_mixed_args(mxe_ctx* c, int max_steps, double t_end) {
+    TubeMixedArgs a{};
+    a.U = c->U;
+    a.W = c->W;
+    a.Ws = c->Ws;
+    a.tubes = c->tdesc_d;
+    a.order = c->order_d;
+    a.queue = c->queue_d;
+    a.clk = c->tclk;
+    a.bc_type[0] = c->bc_type[0];
+    a.bc_type[1] = c->bc_type[1];
+    a.ghost = c->ghost_d;
+    a.ntubes = c->ntubes;
+    a.integrator = c->cfg.integrator;
+    a.max_steps = max_steps;
+    a.resync_every = c->resync_every;
+    a.cfl = c->cfg.cfl;
+    a.t_end = t_end;
+    a.sl64 = c->sp.sigma_lim;
+    a.kw64 = c->sp.k_ws;
+    return a;
+}
+
+// Launch shape of the persistent tube kernel with nt threads per CTA and
+// teams of cl CTAs (a cluster when cl > 1): as many teams as can be
+// resident at once, at most one per tube.
+struct TubeLaunch {
+    const void* kern;
+    size_t smem;
+    int nt, cl, teams;
+};
+
+static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
+    const bool pl = tubes_planar(c);
+    L->kern = tubes_mixed_kernel(pl, nt);
+    L->smem = tubes_mixed_smem(pl, nt);
+    L->nt = nt;
+    L->cl = cl;
+    int teams = 0;
+    if (cl > 1) {
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        lc.blockDim = dim3(nt, 1, 1);
+        lc.dynamicSmemBytes = L->smem;
+        lc.gridDim = dim3(cl * c->ntubes, 1, 1);
+        CK(cudaOccupancyMaxActiveClusters(&teams, L->kern, &lc));
+    } else {
+        int per = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, L->kern, nt, L->smem));
+        teams = per * c->nsm;
+    }
+    if (teams < 1) return fail(c, MXE_ECUDA, "tube block shape %d x %d does not fit", nt, cl);
+    L->teams = std::min(teams, c->ntubes);
+    return MXE_OK;
+}
+
+// Queue reset + one persistent launch on `st` (no other runtime call, so it
+// can be captured into a graph).
+static mxe_status launch_tubes_mixed(mxe_ctx* c, cudaStream_t st, const TubeMixedArgs& a,
+                                     const TubeLaunch& L) {
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    lc.blockDim = dim3(L.nt, 1, 1);
+    lc.gridDim = dim3(L.cl * L.teams, 1, 1);
+    lc.dynamicSmemBytes = L.smem;
+    lc.stream = st;
+    if (L.cl > 1) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = L.cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+    }
+    ParamsT<float> p = fparams(c);
+    MixedPolicy mp = c->mp;
+    void* args[] = {(void*)&a, (void*)&p, (void*)&mp};
+    CK(cudaMemsetAsync(c->queue_d, 0, sizeof(int), st));
+    CK(cudaLaunchKernelExC(&lc, L.kern, args));
+    return MXE_OK;
+}
+
+// Run through the cached CUDA graph [queue reset, persistent launch]; the
+// graph is captured again when t_end, max_steps, the block shape or any
+// launch argument changed.
+static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const double* dts,
+                                  int ndts) {
+    TubeLaunch L;
+    mxe_status s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L);
+    if (s != MXE_OK) return s;
+    if (dts) {                                   // prescribed steps: direct launch
+        s = upload_dts(c, dts, ndts);
+        if (s != MXE_OK) return s;
+        TubeMixedArgs a = tubes_mixed_args(c, ndts, INFINITY);
+        a.dt_fixed = c->dts_d;
+        a.n_fixed = ndts;
+        return launch_tubes_mixed(c, c->stream, a, L);
+    }
+    if (!c->gexec || c->g_tend != t_end || c->g_steps != max_steps || c->g_nt != c->tune_nt ||
+        c->g_cl != c->tune_cl || c->g_gen != c->gen) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        TubeMixedArgs a = tubes_mixed_args(c, max_steps, t_end);
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s = launch_tubes_mixed(c, c->cap_stream, a, L);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (s != MXE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(c, MXE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, MXE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        c->g_tend = t_end;
+        c->g_steps = max_steps;
+        c->g_nt = c->tune_nt;
+        c->g_cl = c->tune_cl;
+        c->g_gen = c->gen;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    return MXE_OK;
+}
+
 static mxe_status run_tubes(mxe_ctx* c, int max_steps, double t_end, const double* dts,
                             int ndts) {
+    if (c->mixed) return run_tubes_mixed(c, max_steps, t_end, dts, ndts);
     TubeArgs a{};
     a.U = c->U;
     a.Us = c->Us;
@@ -686,14 +874,8 @@ static mxe_status run_tubes(mxe_ctx* c, int max_steps, double t_end, const doubl
     a.t_end = t_end;
     a.max_steps = max_steps;
     if (dts) {
-        if (ndts > c->dts_cap) {
-            cudaFree(c->dts_d);
-            c->dts_d = nullptr;
-            CK(cudaMalloc(&c->dts_d, sizeof(double) * ndts));
-            c->dts_cap = ndts;
-        }
-        CK(cudaMemcpyAsync(c->dts_d, dts, sizeof(double) * ndts, cudaMemcpyHostToDevice,
-                           c->stream));
+        mxe_status s = upload_dts(c, dts, ndts);
+        if (s != MXE_OK) return s;
         a.dt_fixed = c->dts_d;
         a.n_fixed = ndts;
         a.max_steps = ndts;
@@ -805,6 +987,7 @@ extern "C" mxe_status mxe_set_mixed_policy(mxe_ctx* c, double sigma_lo, double s
         return fail(c, MXE_EINVAL, "bad mixed-precision policy");
     c->mp = MixedPolicy{(float)sigma_lo, (float)sigma_hi, (float)det_min};
     c->resync_every = resync_every;
+    ++c->gen;
     return MXE_OK;
 }
 
@@ -825,6 +1008,92 @@ extern "C" mxe_status mxe_batch_get_clock(mxe_ctx* c, double* t, long long* step
         if (t) t[b] = h[b].t;
         if (steps) steps[b] = h[b].steps;
     }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_autotune(mxe_ctx* c, double t_probe, int* nt_out, int* cl_out,
+                                         double* ms_out) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes || !c->mixed) return fail(c, MXE_ESTATE, "autotuning needs an MXE_MIXED 1D context");
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    if (!(t_probe > 0.0) || !std::isfinite(t_probe)) return fail(c, MXE_EINVAL, "t_probe must be > 0");
+    mxe_status s = periodic_ok(c);
+    if (s != MXE_OK) return s;
+    // save the state and the clocks; every candidate starts from them
+    std::vector<TubeClock> ck(c->ntubes);
+    CK(cudaMemcpyAsync(ck.data(), c->tclk, sizeof(TubeClock) * c->ntubes, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double t0 = 0.0;
+    for (const TubeClock& k : ck) t0 = std::max(t0, k.t);
+    double* Usave = nullptr;
+    CK(cudaMalloc(&Usave, sizeof(double) * c->nelem));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Usave, c->U, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    const int nts[2] = {128, 256}, cls[4] = {1, 2, 4, 8};
+    float best = INFINITY;
+    int bnt = c->tune_nt, bcl = c->tune_cl;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        for (int j = 0; j < 4 && e == cudaSuccess; ++j) {
+            TubeLaunch L;
+            if (tube_launch_shape(c, nts[i], cls[j], &L) != MXE_OK) {
+                cudaGetLastError();
+                continue;                       // shape does not fit on this device
+            }
+            e = cudaMemcpyAsync(c->U, Usave, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
+                                c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->tclk, ck.data(), sizeof(TubeClock) * c->ntubes,
+                                    cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            if (e != cudaSuccess) break;
+            TubeMixedArgs a = tubes_mixed_args(c, 1 << 30, t0 + t_probe);
+            if (launch_tubes_mixed(c, c->stream, a, L) != MXE_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                bnt = nts[i];
+                bcl = cls[j];
+            }
+        }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->U, Usave, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tclk, ck.data(), sizeof(TubeClock) * c->ntubes,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(Usave);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(c, MXE_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    if (!(best < INFINITY)) return fail(c, MXE_ECUDA, "autotune: no block shape could be launched");
+    c->tune_nt = bnt;
+    c->tune_cl = bcl;
+    c->tuned = true;
+    if (nt_out) *nt_out = bnt;
+    if (cl_out) *cl_out = bcl;
+    if (ms_out) *ms_out = best;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_set_shape(mxe_ctx* c, int nt, int cl) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes || !c->mixed) return fail(c, MXE_ESTATE, "block shapes apply to MXE_MIXED 1D contexts");
+    if ((nt != 128 && nt != 256) || (cl != 1 && cl != 2 && cl != 4 && cl != 8))
+        return fail(c, MXE_EINVAL, "shape must be nt in {128, 256}, cl in {1, 2, 4, 8}");
+    c->tune_nt = nt;
+    c->tune_cl = cl;
     return MXE_OK;
 }
 
@@ -857,6 +1126,11 @@ extern "C" mxe_status mxe_get_diagnostics(mxe_ctx* c, mxe_diag* out) {
         out->last_dt = h[0].last_dt;
         out->steps = h[0].steps;
         out->max_rate = h[0].rate;
+        for (const TubeClock& k : h) {
+            out->n_fp64_closures += (long long)k.n_face64;
+            out->n_closures += (long long)k.n_face;
+        }
+        out->planar = (c->mixed && tubes_planar(c)) ? 1 : 0;
     } else {
         DevClock h{};
         mxe_status s = read_clock_2d(c, &h);

@@ -21,7 +21,7 @@
 // shared memory, one thread per face; instantiated for the general and the
 // planar (ten-moment) state.
 #include "mxe_internal.h"
-#include "mxe_policy.cuh"
+#include "mxe_mixed.cuh"
 
 namespace mxe {
 
@@ -31,9 +31,7 @@ constexpr int NBOXm = BXm * BYm;
 constexpr int NPHXm = (TXm + 2) * TYm;
 constexpr int NPHYm = TXm * (TYm + 2);
 
-struct MixedPolicy {
-    float sig_lo, sig_hi, det_min;
-};
+
 
 __device__ __forceinline__ const double* map_cell_m(const Grid2D& g, int& gi, int& gj) {
     bool xin = (gi >= 0 && gi < g.nx), yin = (gj >= 0 && gj < g.ny);
@@ -78,47 +76,6 @@ __device__ __forceinline__ void load_prim_f32(const Stage2DArgs& a, int gi, int 
     const float* p = a.Win + (long long)gj * g.pitch + gi;
 #pragma unroll
     for (int k = 0; k < PH::NF; ++k) Q[k] = __ldg(p + k * g.fstride);
-}
-
-// FP64 re-evaluation of one face state (kept out of line: rare path)
-template <class PH, int K>
-__device__ __noinline__ void face_fp64(const float* Qf, double sl, double kw, float* out) {
-    constexpr int NF = PH::NF;
-    double Q[NF], U[NF], F[NF], lo, hi;
-#pragma unroll
-    for (int k = 0; k < NF; ++k) Q[k] = (double)Qf[k];
-    PH::template face<double, K>(Q, sl, kw, U, F, lo, hi);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        out[k] = (float)U[k];
-        out[NF + k] = (float)F[k];
-    }
-    out[2 * NF] = (float)lo;
-    out[2 * NF + 1] = (float)hi;
-}
-
-// One face state: conserved U, flux F, wave speeds (out[2NF], out[2NF+1]);
-// FP64 re-evaluation where the closure is ill-conditioned.
-template <class PH, int K>
-__device__ __forceinline__ bool face_state_m(const float* Qf, const ParamsT<float>& p,
-                                             const MixedPolicy& mp, double sl64, double kw64,
-                                             float* out) {
-    constexpr int NF = PH::NF;
-    float lo, hi;
-    PH::template face<float, K>(Qf, p.sigma_lim, p.k_ws, out, out + NF, lo, hi);
-    out[2 * NF] = lo;
-    out[2 * NF + 1] = hi;
-    bool flag = false;
-    if (mp.sig_lo > 0.0f || mp.sig_hi < 1.0f || mp.det_min > 0.0f) {
-        float sig, det;
-        PH::conditioning(Qf, sig, det);
-        flag = (sig >= p.sigma_lim && sig < mp.sig_lo) || sig > mp.sig_hi || det < mp.det_min ||
-               !(sig == sig);
-        if (__any_sync(__activemask(), flag)) {
-            if (flag) face_fp64<PH, K>(Qf, sl64, kw64, out);
-        }
-    }
-    return flag;
 }
 
 template <int NF>

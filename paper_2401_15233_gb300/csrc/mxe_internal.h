@@ -62,6 +62,7 @@ struct Stage2DArgs {
 // ---- 1D tubes ----
 struct TubeDesc {
     long long off;                  // element offset of the tube's field 0
+    long long coff;                 // cell offset (cells of the tubes before it)
     int n;                          // cells
     int pad;
     double dx;
@@ -88,6 +89,27 @@ struct TubeArgs {
     SchemeParams sp;
     double cfl, t_end;
     int max_steps;
+    const double* dt_fixed;         // NULL, or n_fixed prescribed steps
+    int n_fixed;
+};
+
+// Mixed-precision batched tubes (one persistent launch, work queue)
+struct TubeMixedArgs {
+    double* U;                      // all tubes, FP64 conserved (14 fields per tube)
+    float* W;                       // FP32 primitives, NF fields per tube at NF * coff
+    float* Ws;                      // FP32 primitives of the stage state (same layout)
+    const TubeDesc* tubes;
+    const int* order;               // tube indices in the order they are handed out
+    int* queue;                     // next position in `order` (zero at launch)
+    TubeClock* clk;
+    int bc_type[2];
+    const double* ghost;            // [2][14] primitive ghost states
+    int ntubes;
+    int integrator;                 // 0 FE, 1 RK2
+    int max_steps;
+    int resync_every;               // W = prim(U) in FP64 every this many steps
+    double cfl, t_end;
+    double sl64, kw64;              // sigma_lim and k for the FP64 re-evaluation
     const double* dt_fixed;         // NULL, or n_fixed prescribed steps
     int n_fixed;
 };

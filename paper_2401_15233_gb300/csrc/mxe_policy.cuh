@@ -63,6 +63,13 @@ struct PhysGeneral {
         ax = amax14<T, 0>(Q, d, sl, kw);
         ay = amax14<T, 1>(Q, d, sl, kw);
     }
+    // x rate alone (1D problems)
+    template <class T>
+    static __device__ __forceinline__ T rate_x(const T* Q, T sl, T kw) {
+        Dimless14<T> d;
+        dimless14(Q, d);
+        return amax14<T, 0>(Q, d, sl, kw);
+    }
     static __device__ __forceinline__ void increment(const float* W, const float* dU, float* Wn) {
         prim_increment14(W, dU, Wn);
     }
@@ -101,6 +108,12 @@ struct PhysPlanar {
         dimless_p(Q, g);
         ax = amax_p<T, 0>(Q, g, sl, kw);
         ay = amax_p<T, 1>(Q, g, sl, kw);
+    }
+    template <class T>
+    static __device__ __forceinline__ T rate_x(const T* Q, T sl, T kw) {
+        DimlessP<T> g;
+        dimless_p(Q, g);
+        return amax_p<T, 0>(Q, g, sl, kw);
     }
     static __device__ __forceinline__ void increment(const float* W, const float* dU, float* Wn) {
         prim_increment_p(W, dU, Wn);
