@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched-tube leg (256 Sod tubes, one graph launch)")
     return p.parse_args()
 
 
@@ -175,6 +177,71 @@ def cpu_baseline(wl, seconds_target=15.0):
             break
     return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n}x{n} crossed jets, {steps} RK2 steps incl. CFL, {el:.1f} s, 1 thread"}
+
+
+def bench_batch(mx, wl, stream, world):
+    """Batched 14-moment Sod tubes: 256 tubes of 512..8192 cells, Kn in
+    [1e-3, 10], density ratio in [4, 20], each run to t = 0.2 in one persistent
+    launch replayed from a CUDA graph, block shape from the autotuner.  Also
+    times the FP64 batch (one block per tube) against the mixed batch over the
+    first 20 steps of every tube, from the same initial state."""
+    import numpy as np
+    import torch
+    tubes = wl.batch_tubes()
+    ncells = np.array([t[0] for t in tubes], dtype=np.int64)
+    prims = [np.ascontiguousarray(np.moveaxis(wl.sod_prim(14, nc, rhoR=1 / r, PR=1 / r), -1, 0))
+             for (nc, kn, r) in tubes]
+
+    def make(prec):
+        b = mx.Batch(list(ncells), [1.0] * len(tubes), system=14, precision=prec, order=2,
+                     integrator="rk2", flux="hll", limiter="minmod", cfl=0.5, sigma_lim=1e-4)
+        b.set_stream(stream.cuda_stream)
+        b.set_state(b.pack(prims))
+        for i, (nc, kn, r) in enumerate(tubes):
+            b.set_tube_relaxation(i, mx.TAU_HARDSPHERE, wl.sod_tau_ref(kn), 1.0, 1.0)
+        return b
+
+    def timed_run(b, t_end, max_steps=10 ** 8):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.run(max_steps, t_end)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t, st = b.clock()
+        return e0.elapsed_time(e1), int((ncells * st).sum()), st
+
+    b = make("mixed")
+    nt, cl, tune_ms = b.autotune(0.002)
+    b.run(10 ** 8, 0.2)                   # warm-up: captures the graph for t_end = 0.2
+    b.set_state(b.pack(prims))            # back to t = 0 (same launch arguments: replay)
+    ms, cu, st = timed_run(b, 0.2)
+    d = b.diagnostics()
+    bw = make("mixed")
+    bw.set_shape(nt, cl)
+    bw.run(20, 0.2)
+    bw.set_state(b.pack(prims))
+    ms_w, cu_w, _ = timed_run(bw, 0.2, 20)
+    del bw
+    bf = make("fp64")
+    bf.run(3, 0.2)
+    bf.set_state(b.pack(prims))
+    ms_f, cu_f, _ = timed_run(bf, 0.2, 20)
+    del bf
+    return {
+        "workload": "batched 14-moment Sod: 256 tubes, 512..8192 cells (log-uniform, seed "
+                    "20240127), Kn 1e-3..10, density ratio 4..20, RK2 MUSCL minmod HLL, to t = 0.2",
+        "precision": "mixed", "value": world * cu / (ms * 1e-3), "unit": UNIT,
+        "ms": ms, "cell_updates": cu, "cells": int(ncells.sum()),
+        "steps_min": int(st.min()), "steps_max": int(st.max()),
+        "graph_launches": 1, "gpu_launches": 2,
+        "shape": {"threads_per_cta": nt, "ctas_per_team": cl, "autotune_ms_t0.002": tune_ms},
+        "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"]) if d["n_closures"] else None,
+        "n_nonfinite": d["n_nonfinite"], "n_nonpositive": d["n_nonpositive"],
+        "first_20_steps": {"mixed": world * cu_w / (ms_w * 1e-3),
+                           "fp64": world * cu_f / (ms_f * 1e-3),
+                           "speedup": (cu_w / ms_w) / (cu_f / ms_f), "unit": UNIT},
+    }
 
 
 def run_reference(args, wl):
@@ -327,6 +394,8 @@ def main():
                  "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"])
                  if d["n_closures"] else None},
     }
+    if not args.no_batch:
+        out["batch"] = bench_batch(mx, wl, stream, world)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(out), flush=True)

@@ -87,6 +87,7 @@ struct mxe_ctx {
     cudaGraphExec_t gexec = nullptr;       // captured [queue reset, persistent launch]
     double g_tend = -1.0;
     int g_steps = -1, g_nt = 0, g_cl = 0;
+    bool g_planar = false;
     long long g_gen = -1;
     long long gen = 0;                // bumped whenever launch arguments change
     // state
@@ -509,7 +510,6 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
     mxe_k_setstate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->U);
     CK(cudaGetLastError());
     c->state_planar = (res[1] == 0ull);
-    ++c->gen;
     if (!c->tubes && c->Us) CK(cudaMemsetAsync(c->Us, 0, sizeof(double) * c->nelem, c->stream));
     mxe_status s = reset_clock(c);
     if (s != MXE_OK) return s;
@@ -824,7 +824,7 @@ static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const
         return launch_tubes_mixed(c, c->stream, a, L);
     }
     if (!c->gexec || c->g_tend != t_end || c->g_steps != max_steps || c->g_nt != c->tune_nt ||
-        c->g_cl != c->tune_cl || c->g_gen != c->gen) {
+        c->g_cl != c->tune_cl || c->g_gen != c->gen || c->g_planar != tubes_planar(c)) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
@@ -850,6 +850,7 @@ static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const
         c->g_nt = c->tune_nt;
         c->g_cl = c->tune_cl;
         c->g_gen = c->gen;
+        c->g_planar = tubes_planar(c);
     }
     CK(cudaGraphLaunch(c->gexec, c->stream));
     return MXE_OK;
