@@ -16,6 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "maxent_oracle.c")
 _LIB = os.path.join(_HERE, "libmaxent_oracle.so")
+_TSRC = os.path.join(_HERE, "tangent.cpp")
+_TLIB = os.path.join(_HERE, "libmaxent_oracle_tangent.so")
 
 BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
 FLUX_HLL, FLUX_RUSANOV = 0, 1
@@ -36,6 +38,19 @@ def build(force: bool = False) -> str:
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
+
+
+def build_tangent(force: bool = False) -> str:
+    """Compile the forward-mode tangent: the same oracle source with a
+    dual-number arithmetic type (g++, no FMA contraction)."""
+    deps = [_SRC, _TSRC, os.path.join(_HERE, "maxent_oracle.h")]
+    if force or not os.path.exists(_TLIB) or os.path.getmtime(_TLIB) < max(
+            os.path.getmtime(d) for d in deps):
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", _TLIB + ".tmp", _TSRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_TLIB + ".tmp", _TLIB)
+    return _TLIB
 
 
 class Side(C.Structure):
@@ -306,3 +321,97 @@ def window_step(cfg: Cfg, U, i0, j0, w, h, dtv):
     jj = np.mod(jj, ny) if per_y else np.clip(jj, 0, ny - 1)
     Ub = U[np.ix_(jj, ii)]
     return block_step(cfg, i0, j0, w, h, Ub, dtv)
+
+
+# ---------------------------------------------------------------- tangent
+_D2 = C.c_double * 2            # one dual number (value, derivative)
+
+
+class SideT(C.Structure):
+    _fields_ = [
+        ("base_type", C.c_int),
+        ("base_state", _D2 * 14),
+        ("nspans", C.c_int),
+        ("span_lo", C.c_double * MAX_SPANS),
+        ("span_hi", C.c_double * MAX_SPANS),
+        ("span_state", (_D2 * 14) * MAX_SPANS),
+    ]
+
+
+class CfgT(C.Structure):
+    _fields_ = [
+        ("system", C.c_int),
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+        ("order", C.c_int), ("integrator", C.c_int), ("flux", C.c_int), ("limiter", C.c_int),
+        ("cfl", C.c_double), ("sigma_lim", C.c_double), ("k_ws", C.c_double),
+        ("tau_model", C.c_int),
+        ("tau_ref", _D2), ("rho_ref", _D2), ("T_ref", _D2),
+        ("side", SideT * 4),
+    ]
+
+
+_tlib = None
+
+
+def tangent_lib():
+    global _tlib
+    if _tlib is None:
+        L = C.CDLL(build_tangent())
+        L.or_tangent_cfg_size.argtypes = []
+        L.or_tangent_cfg_size.restype = C.c_size_t
+        assert L.or_tangent_cfg_size() == C.sizeof(CfgT), "dual cfg layout mismatch"
+        L.or_tangent_run.argtypes = [C.POINTER(CfgT), _dp, _dp, C.c_int, _dp, _dp, _dp]
+        L.or_tangent_run.restype = C.c_int
+        L.or_tangent_residual.argtypes = [C.POINTER(CfgT), _dp, _dp, _dp, _dp]
+        L.or_tangent_residual.restype = C.c_int
+        _tlib = L
+    return _tlib
+
+
+def tangent_cfg(cfg: Cfg, d_states=None, d_tau_ref=0.0, d_rho_ref=0.0, d_T_ref=0.0) -> CfgT:
+    """Dual configuration: cfg's values with derivative directions for the
+    imposed boundary states (d_states[s][0] = base state of side s,
+    d_states[s][1 + n] = span n; primitive vectors of 14) and the
+    relaxation parameters."""
+    t = CfgT()
+    for name in ("system", "nx", "ny", "x0", "x1", "y0", "y1", "order", "integrator", "flux",
+                 "limiter", "cfl", "sigma_lim", "k_ws", "tau_model"):
+        setattr(t, name, getattr(cfg, name))
+    for name, dv in (("tau_ref", d_tau_ref), ("rho_ref", d_rho_ref), ("T_ref", d_T_ref)):
+        getattr(t, name)[0] = getattr(cfg, name)
+        getattr(t, name)[1] = dv
+    ds = np.zeros((4, 1 + MAX_SPANS, 14)) if d_states is None else np.asarray(d_states, float)
+    for s in range(4):
+        sd, st = cfg.side[s], t.side[s]
+        st.base_type, st.nspans = sd.base_type, sd.nspans
+        for k in range(14):
+            st.base_state[k][0] = sd.base_state[k]
+            st.base_state[k][1] = ds[s, 0, k]
+        for n in range(MAX_SPANS):
+            st.span_lo[n], st.span_hi[n] = sd.span_lo[n], sd.span_hi[n]
+            for k in range(14):
+                st.span_state[n][k][0] = sd.span_state[n][k]
+                st.span_state[n][k][1] = ds[s, 1 + n, k]
+    return t
+
+
+def tangent_run(tcfg: CfgT, U, dU, dts):
+    """n = len(dts) steps of the given sizes from U (ny, nx, nf) in the
+    direction dU (and tcfg's directions).  Returns (U_n, dU_n)."""
+    U = _a(U).reshape(tcfg.ny, tcfg.nx, -1)
+    out, dout = np.empty_like(U), np.empty_like(U)
+    dts = _a(dts)
+    tangent_lib().or_tangent_run(C.byref(tcfg), U.reshape(-1), _a(dU).reshape(-1), len(dts),
+                                 dts if len(dts) else np.zeros(1), out.reshape(-1),
+                                 dout.reshape(-1))
+    return out, dout
+
+
+def tangent_residual(tcfg: CfgT, U, dU):
+    """(L(U), dL) for non-periodic sides: the residual and its derivative."""
+    U = _a(U).reshape(tcfg.ny, tcfg.nx, -1)
+    L, dL = np.empty_like(U), np.empty_like(U)
+    tangent_lib().or_tangent_residual(C.byref(tcfg), U.reshape(-1), _a(dU).reshape(-1),
+                                      L.reshape(-1), dL.reshape(-1))
+    return L, dL

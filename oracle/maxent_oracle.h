@@ -26,6 +26,15 @@
 #ifndef MAXENT_ORACLE_H
 #define MAXENT_ORACLE_H
 
+/* Type of the physical quantities held by the configuration (imposed
+ * boundary states, relaxation parameters): double, except in the tangent
+ * build, which substitutes a dual-number type. */
+#ifndef OR_REAL
+#define OR_REAL double
+#endif
+typedef OR_REAL or_real;
+
+#ifndef OR_TANGENT_BUILD
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -63,6 +72,11 @@ void   or14_source(const double *Q, double tau, double *C);
 void   or_prim2cons_n(int nf, long n, const double *Q, double *U);
 void   or_cons2prim_n(int nf, long n, const double *U, double *Q);
 
+#ifdef __cplusplus
+}
+#endif
+#endif /* OR_TANGENT_BUILD */
+
 /* ---------------- finite-volume scheme ---------------- */
 enum { OR_BC_TRANSMISSIVE = 0, OR_BC_PERIODIC = 1, OR_BC_DIRICHLET = 2 };
 enum { OR_FLUX_HLL = 0, OR_FLUX_RUSANOV = 1 };
@@ -73,10 +87,10 @@ enum { OR_FE = 0, OR_RK2 = 1 };
 
 typedef struct {
     int    base_type;                 /* OR_BC_* for the whole side        */
-    double base_state[14];            /* primitive state if DIRICHLET      */
+    or_real base_state[14];           /* primitive state if DIRICHLET      */
     int    nspans;                    /* Dirichlet spans overriding base   */
     double span_lo[OR_MAX_SPANS], span_hi[OR_MAX_SPANS];
-    double span_state[OR_MAX_SPANS][14];
+    or_real span_state[OR_MAX_SPANS][14];
 } or_side;
 
 typedef struct {
@@ -89,7 +103,7 @@ typedef struct {
     int    limiter;       /* OR_LIM_*                                      */
     double cfl, sigma_lim, k_ws;
     int    tau_model;     /* OR_TAU_*                                      */
-    double tau_ref, rho_ref, T_ref;
+    or_real tau_ref, rho_ref, T_ref;
     or_side side[4];      /* 0 xlo, 1 xhi, 2 ylo, 3 yhi                    */
 } or_cfg;
 
@@ -100,6 +114,11 @@ typedef struct {
  * boundary are filled from the boundary conditions; the other sides must
  * carry real neighbour data in all 4 margin layers. */
 #define OR_MARGIN 4
+
+#ifndef OR_TANGENT_BUILD
+#ifdef __cplusplus
+extern "C" {
+#endif
 
 /* One time step of size dt on a block.  Ub is the block with margins
  * (size (w+2M)*(h+2My)*nf); Uout receives the w*h interior cells.
@@ -127,4 +146,5 @@ double or_tau(const or_cfg *c, const double *Q);
 #ifdef __cplusplus
 }
 #endif
+#endif /* OR_TANGENT_BUILD */
 #endif
