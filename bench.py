@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-tube leg (256 Sod tubes, one graph launch)")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the adjoint leg (512^2 crossed jets, 500 steps, checkpoints every 50)")
     return p.parse_args()
 
 
@@ -244,6 +246,57 @@ def bench_batch(mx, wl, stream, world):
     }
 
 
+def bench_adjoint(world):
+    """Discrete adjoint of the crossed jets, 512^2, Kn = 0.1, 500 RK2 steps
+    from the background at rest, checkpoints every 50 steps: gradient of the
+    mean density over the central 32 x 32 probe w.r.t. both Mach numbers and
+    tau_ref.  Cost ratio = (forward with checkpoints + backward with
+    recomputation) / plain forward, host wall time around device-synchronised
+    work.  Gradients are compared with central differences of the frozen-dt
+    map (h = 1e-4 on the Mach numbers, 1e-4 relative on tau_ref), for MUSCL
+    (the configuration) and for first-order reconstruction."""
+    import numpy as np
+    import torch
+    from paper_2401_15233_gb300 import adjoint as ad
+    out = {"workload": "crossed jets 512x512, Kn 0.1, 500 RK2 steps from rest, checkpoints "
+                       "every 50, probe 32x32 at the centre; FP64"}
+    w = ad.JetsProblem(n=64, nsteps=20, ckpt=10, probe=8, initial="rest")
+    Jw, c, d, sw = ad.forward_checkpointed(w, w.params0())      # warm-up
+    ad.backward_checkpointed(w, sw, c, d)
+    for order in (2, 1):
+        prob = ad.JetsProblem(n=512, nsteps=500, ckpt=50, probe=32, initial="rest", order=order)
+        p0 = prob.params0()
+        s = prob.solver(p0)
+        s.set_state(prob.initial())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(prob.nsteps, float("inf"))
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        del s
+        t0 = time.perf_counter()
+        J, ckpts, dts, s2 = ad.forward_checkpointed(prob, p0)
+        torch.cuda.synchronize()
+        tfc = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        g, _ = ad.backward_checkpointed(prob, s2, ckpts, dts)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        fd = []
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-4 * (p0[2] if k == 2 else 1.0)
+            fd.append((ad.run_fixed(prob, p0 + e, dts) - ad.run_fixed(prob, p0 - e, dts)) / (2 * e[k]))
+        out["muscl" if order == 2 else "first_order"] = {
+            "forward_s": tf, "forward_ckpt_s": tfc, "backward_s": tb, "ratio": (tfc + tb) / tf,
+            "t_final": float(dts.sum()), "J": J, "grad": [float(x) for x in g],
+            "fd": [float(x) for x in fd], "probe_at_background": J == prob.setup["background"][0],
+        }
+        del s2, ckpts
+    out["ratio"] = out["muscl"]["ratio"]
+    return out
+
+
 def run_reference(args, wl):
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
@@ -396,6 +449,8 @@ def main():
     }
     if not args.no_batch:
         out["batch"] = bench_batch(mx, wl, stream, world)
+    if not args.no_adjoint:
+        out["adjoint"] = bench_adjoint(world)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(out), flush=True)

@@ -61,7 +61,7 @@ enum { MXE_FE = 0, MXE_RK2 = 1 };                     /* Sec. 3               */
 enum { MXE_BC_TRANSMISSIVE = 0, MXE_BC_PERIODIC = 1, MXE_BC_DIRICHLET = 2 };
 enum { MXE_SIDE_XLO = 0, MXE_SIDE_XHI = 1, MXE_SIDE_YLO = 2, MXE_SIDE_YHI = 3 };
 enum { MXE_TAU_NONE = 0, MXE_TAU_CONST = 1, MXE_TAU_HARDSPHERE = 2 };
-enum { MXE_PRIMITIVE = 0, MXE_CONSERVED = 1, MXE_SIGMA = 2 };
+enum { MXE_PRIMITIVE = 0, MXE_CONSERVED = 1, MXE_SIGMA = 2, MXE_CONSERVED_RESTORE = 3 };
 
 typedef struct {
     int    system;       /* 5 (1D1V, Sec. 2.3) or 14 (3D3V, Sec. 2.4)            */
@@ -123,7 +123,10 @@ void      *mxe_get_stream(const mxe_ctx *ctx);
  * is a device pointer.  Resets t = 0 and the step count.  Every cell is
  * checked (rho > 0, finite, positive pressure); a failing state returns
  * MXE_EUNREALIZABLE with the first offending cell in the message and
- * leaves the previous state in place. */
+ * leaves the previous state in place.  Kind CONSERVED_RESTORE takes a
+ * conserved state verbatim without the realizability check: it restores a
+ * state this solver produced (a checkpoint read with mxe_get_moments),
+ * which the scheme itself may have left slightly outside sigma <= 1. */
 mxe_status mxe_set_state(mxe_ctx *ctx, int kind, const double *soa, int on_device);
 
 /* Read the state into a SoA array (kind PRIMITIVE, CONSERVED; or SIGMA: one
@@ -220,6 +223,48 @@ mxe_status mxe_batch_autotune(mxe_ctx *ctx, double t_probe, int *nt_out, int *cl
 /* MXE_MIXED tube contexts: set the block shape directly (nt in {128, 256},
  * cl in {1, 2, 4, 8}); the default is 128 x 1. */
 mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
+
+/* ---- time-step history (2D grids) --------------------------------------- */
+
+/* Keep the dt of every step in a device buffer of `capacity` entries
+ * (entry s = step s counted from the last mxe_set_state; later steps are
+ * not kept); 0 switches it off.  Synchronises; MXE_ESTATE for 1D contexts. */
+mxe_status mxe_set_dt_history(mxe_ctx *ctx, long long capacity);
+
+/* Copy the first n kept step sizes to the host array out (synchronises).
+ * MXE_EINVAL if n exceeds the capacity. */
+mxe_status mxe_get_dt_history(mxe_ctx *ctx, long long n, double *out);
+
+/* ---- discrete adjoint (2D 14-moment, planar state, MXE_FP64) ------------ */
+
+/* Sec. 3 scheme as a map U^{n+1} = Phi(U^n; imposed boundary states, tau_ref)
+ * with the step sizes held fixed.  mxe_adjoint_record advances the current
+ * state by n steps of the given sizes (as mxe_step_dt) and keeps U^n and,
+ * for RK2, U* of every step on the device (the tape: 2 n copies of the
+ * state; replaces the previous tape).  The context must hold a planar
+ * state (u_z, P_xz, P_yz, q_z zero) and planar boundary states.
+ * Errors: MXE_ESTATE (not an FP64 2D 14-moment planar context, no state),
+ * MXE_EINVAL (n < 1, dt <= 0), MXE_ENOMEM / MXE_ECUDA. */
+mxe_status mxe_adjoint_record(mxe_ctx *ctx, int n, const double *dts);
+
+/* Reverse sweep over the tape (hand-written reverse mode of primitive
+ * recovery, shared limiter + MUSCL, closure, wave speeds, HLL / Rusanov and
+ * the BGK source; branches as taken by the primal).  ubar (dense
+ * (14, ny, nx), host or device per on_device) holds on entry the adjoint of
+ * the state after the last recorded step and receives the adjoint of the
+ * state before the first.  Adds to gbar ([4][1 + MAX_SPANS][14] host
+ * array: side, slot 0 = base Dirichlet state / 1 + n = span n, primitive
+ * field) the adjoint of the imposed primitive states, and to *taubar the
+ * adjoint of tau_ref (either may be NULL).  Synchronises. */
+mxe_status mxe_adjoint_run(mxe_ctx *ctx, double *ubar, int on_device, double *gbar,
+                           double *taubar);
+
+/* Adjoint of the residual L(U) = -div F + C at the conserved state U
+ * (dense (14, ny, nx)): out = (dL/dU)^T V, and adds (dL/dg)^T V to gbar
+ * and (dL/dtau_ref)^T V to *taubar.  For checking the reverse sweep one
+ * residual at a time; allocates a temporary per call; synchronises. */
+mxe_status mxe_adjoint_residual(mxe_ctx *ctx, const double *U, const double *V, double *out,
+                                int on_device, double *gbar, double *taubar);
 
 /* ---- fixed-scratch 1D solve (allocates nothing) -------------------------- */
 

@@ -633,6 +633,13 @@ static void face_state(const or_cfg *c, const real *Qm, const real *Q0,
     }
     real phi = shared_phi(c, Qm, Q0, Qp);
     for (int k = 0; k < nf; ++k) {
+        /* a field that is flat across the stencil keeps its cell value (its
+         * slope phi * 0 vanishes; written out so that its derivative is the
+         * zero slope as well, reading of Sec. 3.2 for the tangent) */
+        if (Q0[k] - Qm[k] == 0.0 && Qp[k] - Q0[k] == 0.0) {
+            Qf[k] = Q0[k];
+            continue;
+        }
         real cen = 0.5 * ((Q0[k] - Qm[k]) + (Qp[k] - Q0[k]));
         Qf[k] = Q0[k] + sgn * 0.5 * (phi * cen);
     }

@@ -24,7 +24,8 @@ __all__ = [
     "mxe_get_moments", "mxe_set_bc", "mxe_set_relaxation", "mxe_step", "mxe_step_dt",
     "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
     "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy", "mxe_tube_run_noalloc",
-    "mxe_batch_autotune", "mxe_batch_set_shape",
+    "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
+    "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
@@ -35,8 +36,9 @@ FE, RK2 = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
 XLO, XHI, YLO, YHI = 0, 1, 2, 3
 TAU_NONE, TAU_CONST, TAU_HARDSPHERE = 0, 1, 2
-PRIMITIVE, CONSERVED, SIGMA = 0, 1, 2
-_KINDS = {"primitive": PRIMITIVE, "conserved": CONSERVED, "sigma": SIGMA}
+PRIMITIVE, CONSERVED, SIGMA, CONSERVED_RESTORE = 0, 1, 2, 3
+_KINDS = {"primitive": PRIMITIVE, "conserved": CONSERVED, "sigma": SIGMA,
+          "restore": CONSERVED_RESTORE}
 
 
 class Config(C.Structure):
@@ -106,6 +108,11 @@ def lib():
             "mxe_batch_autotune": ([_P, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                     C.POINTER(C.c_double)], C.c_int),
             "mxe_batch_set_shape": ([_P, C.c_int, C.c_int], C.c_int),
+            "mxe_set_dt_history": ([_P, C.c_longlong], C.c_int),
+            "mxe_get_dt_history": ([_P, C.c_longlong, _P], C.c_int),
+            "mxe_adjoint_record": ([_P, C.c_int, _P], C.c_int),
+            "mxe_adjoint_run": ([_P, _P, C.c_int, _P, _P], C.c_int),
+            "mxe_adjoint_residual": ([_P, _P, _P, _P, C.c_int, _P, _P], C.c_int),
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
             "mxe_tube_run_noalloc": ([C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_double, _P, C.c_double, C.c_double,
@@ -254,6 +261,48 @@ def mxe_batch_run(ctx, max_steps, t_end):
     _check(ctx, lib().mxe_batch_run(ctx, max_steps, t_end))
 
 
+GHOST_SLOTS = 5                  # base Dirichlet state + 4 spans per side
+
+
+def mxe_set_dt_history(ctx, capacity):
+    _check(ctx, lib().mxe_set_dt_history(ctx, int(capacity)))
+
+
+def mxe_get_dt_history(ctx, n):
+    out = np.empty(int(n))
+    _check(ctx, lib().mxe_get_dt_history(ctx, int(n), C.c_void_p(out.ctypes.data)))
+    return out
+
+
+def mxe_adjoint_record(ctx, dts):
+    d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    _check(ctx, lib().mxe_adjoint_record(ctx, len(d), C.c_void_p(d.ctypes.data)))
+
+
+def mxe_adjoint_run(ctx, ubar):
+    """ubar: adjoint of the final state (numpy or CUDA tensor, (14, ny, nx)),
+    overwritten with the adjoint of the first recorded state.  Returns
+    (gbar [4, GHOST_SLOTS, 14], taubar)."""
+    p, dev = _ptr(ubar)
+    gb = np.zeros((4, GHOST_SLOTS, 14))
+    tb = C.c_double(0.0)
+    _check(ctx, lib().mxe_adjoint_run(ctx, p, dev, C.c_void_p(gb.ctypes.data), C.byref(tb)))
+    return gb, tb.value
+
+
+def mxe_adjoint_residual(ctx, U, V, out):
+    pu, du = _ptr(U)
+    pv, dv = _ptr(V)
+    po, do = _ptr(out)
+    if not (du == dv == do):
+        raise ValueError("U, V and out must all be on the host or all on the device")
+    gb = np.zeros((4, GHOST_SLOTS, 14))
+    tb = C.c_double(0.0)
+    _check(ctx, lib().mxe_adjoint_residual(ctx, pu, pv, po, du, C.c_void_p(gb.ctypes.data),
+                                           C.byref(tb)))
+    return out, gb, tb.value
+
+
 def mxe_batch_autotune(ctx, t_probe):
     nt, cl, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
     _check(ctx, lib().mxe_batch_autotune(ctx, t_probe, C.byref(nt), C.byref(cl), C.byref(ms)))
@@ -331,6 +380,23 @@ class Solver:
 
     def diagnostics(self):
         return mxe_get_diagnostics(self.ctx)
+
+    def set_dt_history(self, capacity):
+        mxe_set_dt_history(self.ctx, capacity)
+
+    def dt_history(self, n):
+        return mxe_get_dt_history(self.ctx, n)
+
+    def adjoint_record(self, dts):
+        mxe_adjoint_record(self.ctx, dts)
+
+    def adjoint_run(self, ubar):
+        return mxe_adjoint_run(self.ctx, ubar)
+
+    def adjoint_residual(self, U, V, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        return mxe_adjoint_residual(self.ctx, U, V, out)
 
     def set_mixed_policy(self, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
         mxe_set_mixed_policy(self.ctx, sigma_lo, sigma_hi, det_min, resync_every)

@@ -44,6 +44,12 @@ extern "C" __global__ void mxe_rate14_2d_mixed_planar(const float* W, Grid2D g,
                                                       DevClock* clk, int slot);
 size_t stage14_2d_mixed_smem(bool planar);
 const void* tubes_mixed_kernel(bool planar, int nt);
+cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
+                      const double* b2, double* out, double* P, double* Cx, double* Cy,
+                      double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
+                      cudaStream_t st);
+extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g,
+                                        int to_pitched);
 size_t tubes_mixed_smem(bool planar, int nt);
 int tile_x();
 int tile_y();
@@ -90,6 +96,20 @@ struct mxe_ctx {
     bool g_planar = false;
     long long g_gen = -1;
     long long gen = 0;                // bumped whenever launch arguments change
+    // dt history of 2D grids (steps counted from set_state)
+    double* dth = nullptr;
+    long long dth_cap = 0;
+    // discrete adjoint: tape of (U^n, U*) per recorded step, scratch
+    double* tape = nullptr;
+    long long tape_cap = 0;           // states the tape can hold
+    int tape_n = 0;                   // recorded steps
+    std::vector<double> tape_dt;
+    double* adjP = nullptr;           // primitives (NP fields, pitched)
+    double* adjCx = nullptr;          // face contributions
+    double* adjCy = nullptr;
+    double* adjA = nullptr;           // adjoint state buffers (pitched)
+    double* adjB = nullptr;
+    double* adjG = nullptr;           // [4][GHOST_SLOTS][14] imposed-state adjoint, then tau_ref's
     // state
     double* U = nullptr;
     double* Us = nullptr;
@@ -394,6 +414,14 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->dts_d);
     cudaFree(c->order_d);
     cudaFree(c->queue_d);
+    cudaFree(c->dth);
+    cudaFree(c->tape);
+    cudaFree(c->adjP);
+    cudaFree(c->adjCx);
+    cudaFree(c->adjCy);
+    cudaFree(c->adjA);
+    cudaFree(c->adjB);
+    cudaFree(c->adjG);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -479,8 +507,10 @@ static mxe_status reset_clock(mxe_ctx* c) {
 extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int on_device) {
     if (!c) return MXE_EINVAL;
     if (!soa) return fail(c, MXE_EINVAL, "soa is NULL");
-    if (kind != MXE_PRIMITIVE && kind != MXE_CONSERVED)
-        return fail(c, MXE_EINVAL, "kind must be PRIMITIVE or CONSERVED");
+    if (kind != MXE_PRIMITIVE && kind != MXE_CONSERVED && kind != MXE_CONSERVED_RESTORE)
+        return fail(c, MXE_EINVAL, "kind must be PRIMITIVE, CONSERVED or CONSERVED_RESTORE");
+    const bool restore = kind == MXE_CONSERVED_RESTORE;
+    if (restore) kind = MXE_CONSERVED;
     size_t bytes = sizeof(double) * c->nf * c->ncell;
     const double* src = soa;
     if (!on_device) {
@@ -498,7 +528,7 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
     CK(cudaMemcpyAsync(res, c->scratch, sizeof res, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     unsigned long long bad = res[0];
-    if (bad != ~0ull) {
+    if (bad != ~0ull && !restore) {
         unsigned long long idx = bad >> 2;
         int code = (int)(bad & 3);
         const char* why = code == 1 ? "non-finite value"
@@ -642,8 +672,13 @@ static mxe_status periodic_ok(mxe_ctx* c) {
     return MXE_OK;
 }
 
-static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed) {
+// One step of a 2D grid.  ustar (FP64 RK2 only, optional): where stage 1
+// writes U* (default: the context's stage buffer).
+static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
+                                 double* ustar = nullptr) {
     Stage2DArgs a{};
+    a.dt_hist = c->dth;
+    a.dt_hist_cap = c->dth_cap;
     a.g = c->g;
     for (int s = 0; s < 4; ++s) a.g.side[s].type = c->bc_type[s];
     a.sp = c->sp;
@@ -685,9 +720,10 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed) {
     auto kern = pl ? mxe_stage14_2d_f64_planar : mxe_stage14_2d_f64;
     size_t smem = stage14_2d_f64_smem(pl);
     if (c->cfg.integrator == MXE_RK2) {
-        a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 0.5; a.final_stage = 0;
+        double* us = ustar ? ustar : c->Us;
+        a.Uin = c->U; a.Ubase = c->U; a.Uout = us; a.coef = 0.5; a.final_stage = 0;
         kern<<<grid, 256, smem, c->stream>>>(a);
-        a.Uin = c->Us; a.Ubase = c->U; a.Uout = c->U; a.coef = 1.0; a.final_stage = 1;
+        a.Uin = us; a.Ubase = c->U; a.Uout = c->U; a.coef = 1.0; a.final_stage = 1;
         kern<<<grid, 256, smem, c->stream>>>(a);
     } else {
         a.Uin = c->U; a.Ubase = c->U; a.Uout = c->Us; a.coef = 1.0; a.final_stage = 1;
@@ -1144,5 +1180,194 @@ extern "C" mxe_status mxe_get_diagnostics(mxe_ctx* c, mxe_diag* out) {
         out->n_closures = (long long)h.n_face;
         out->planar = use_planar(c) ? 1 : 0;
     }
+    return MXE_OK;
+}
+
+// ---------------------------------------------------------------- dt history
+extern "C" mxe_status mxe_set_dt_history(mxe_ctx* c, long long capacity) {
+    if (!c) return MXE_EINVAL;
+    if (c->tubes) return fail(c, MXE_ESTATE, "dt history is kept for 2D grids");
+    if (capacity < 0) return fail(c, MXE_EINVAL, "capacity < 0");
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->dth);
+    c->dth = nullptr;
+    c->dth_cap = 0;
+    if (capacity > 0) {
+        CK(cudaMalloc(&c->dth, sizeof(double) * capacity));
+        CK(cudaMemset(c->dth, 0, sizeof(double) * capacity));
+        c->dth_cap = capacity;
+    }
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_get_dt_history(mxe_ctx* c, long long n, double* out) {
+    if (!c || !out) return MXE_EINVAL;
+    if (n < 0 || n > c->dth_cap) return fail(c, MXE_EINVAL, "n outside the history capacity");
+    if (n == 0) return MXE_OK;
+    CK(cudaMemcpyAsync(out, c->dth, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MXE_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+static mxe_status adjoint_ready(mxe_ctx* c) {
+    if (c->tubes || c->nf != 14 || c->mixed)
+        return fail(c, MXE_ESTATE, "the adjoint needs an MXE_FP64 2D 14-moment context");
+    if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
+    if (!use_planar(c))
+        return fail(c, MXE_ESTATE, "the adjoint needs a planar state (u_z, P_xz, P_yz, q_z zero)");
+    mxe_status s = periodic_ok(c);
+    if (s != MXE_OK) return s;
+    const long long fs = c->g.fstride;
+    if (!c->adjP) {
+        CK(cudaMalloc(&c->adjP, sizeof(double) * NP * fs));
+        CK(cudaMalloc(&c->adjCx, sizeof(double) * 4 * NP * c->g.ny * (long long)(c->g.nx + 1)));
+        CK(cudaMalloc(&c->adjCy, sizeof(double) * 4 * NP * (long long)(c->g.ny + 1) * c->g.nx));
+        CK(cudaMalloc(&c->adjA, sizeof(double) * c->nelem));
+        CK(cudaMalloc(&c->adjB, sizeof(double) * c->nelem));
+        CK(cudaMalloc(&c->adjG, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1)));
+    }
+    return MXE_OK;
+}
+
+static Grid2D adj_grid(const mxe_ctx* c) {
+    Grid2D g = c->g;
+    for (int s = 0; s < 4; ++s) g.side[s].type = c->bc_type[s];
+    return g;
+}
+
+extern "C" mxe_status mxe_adjoint_record(mxe_ctx* c, int n, const double* dts) {
+    if (!c) return MXE_EINVAL;
+    if (n < 1 || !dts) return fail(c, MXE_EINVAL, "need n >= 1 step sizes");
+    for (int i = 0; i < n; ++i)
+        if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return fail(c, MXE_EINVAL, "dt[%d] <= 0", i);
+    mxe_status s = adjoint_ready(c);
+    if (s != MXE_OK) return s;
+    const bool rk2 = c->cfg.integrator == MXE_RK2;
+    const long long need = (long long)n * (rk2 ? 2 : 1);
+    if (need > c->tape_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->tape);
+        c->tape = nullptr;
+        c->tape_cap = 0;
+        CK(cudaMalloc(&c->tape, sizeof(double) * c->nelem * need));
+        c->tape_cap = need;
+    }
+    for (int i = 0; i < n; ++i) {
+        double* un = c->tape + c->nelem * (long long)(rk2 ? 2 * i : i);
+        CK(cudaMemcpyAsync(un, c->U, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        s = launch_2d_step(c, INFINITY, dts[i], rk2 ? un + c->nelem : nullptr);
+        if (s != MXE_OK) return s;
+    }
+    c->tape_n = n;
+    c->tape_dt.assign(dts, dts + n);
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, double* gbar,
+                                      double* taubar) {
+    if (!c) return MXE_EINVAL;
+    if (!ubar) return fail(c, MXE_EINVAL, "ubar is NULL");
+    mxe_status s = adjoint_ready(c);
+    if (s != MXE_OK) return s;
+    if (c->tape_n < 1) return fail(c, MXE_ESTATE, "no recorded steps");
+    const size_t bytes = sizeof(double) * 14 * c->ncell;
+    const double* src = ubar;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->stage, ubar, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->stage;
+    }
+    const Grid2D g = adj_grid(c);
+    const dim3 pg((g.nx + 127) / 128, g.ny);
+    CK(cudaMemsetAsync(c->adjA, 0, sizeof(double) * c->nelem, c->stream));
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(src, c->adjA, g, 1);
+    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1), c->stream));
+    double* gb = c->adjG;
+    double* tb = c->adjG + 4 * GHOST_SLOTS * 14;
+    const ParamsT<double> p = make_params<double>(c->sp, c->rp);
+    const bool rk2 = c->cfg.integrator == MXE_RK2;
+    for (int i = c->tape_n - 1; i >= 0; --i) {
+        const double dt = c->tape_dt[i];
+        const double* un = c->tape + c->nelem * (long long)(rk2 ? 2 * i : i);
+        cudaError_t e;
+        if (rk2) {
+            // U^{n+1} = U^n + dt L(U*): B = dt L'(U*)^T A
+            e = adj_stage(un + c->nelem, c->adjA, dt, nullptr, nullptr, c->adjB, c->adjP,
+                          c->adjCx, c->adjCy, gb, tb, g, p, c->stream);
+            // U* = U^n + dt/2 L(U^n): A = A + B + dt/2 L'(U^n)^T B
+            if (e == cudaSuccess)
+                e = adj_stage(un, c->adjB, 0.5 * dt, c->adjA, c->adjB, c->adjA, c->adjP,
+                              c->adjCx, c->adjCy, gb, tb, g, p, c->stream);
+        } else {
+            e = adj_stage(un, c->adjA, dt, c->adjA, nullptr, c->adjA, c->adjP, c->adjCx,
+                          c->adjCy, gb, tb, g, p, c->stream);
+        }
+        if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint stage: %s", cudaGetErrorString(e));
+    }
+    double* dst = on_device ? ubar : c->stage;
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, c->adjA, g, 0);
+    CK(cudaGetLastError());
+    if (!on_device)
+        CK(cudaMemcpyAsync(ubar, c->stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    double hg[4 * GHOST_SLOTS * 14 + 1];
+    CK(cudaMemcpyAsync(hg, c->adjG, sizeof hg, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (gbar)
+        for (int k = 0; k < 4 * GHOST_SLOTS * 14; ++k) gbar[k] += hg[k];
+    if (taubar) *taubar += hg[4 * GHOST_SLOTS * 14];
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const double* V,
+                                           double* out, int on_device, double* gbar,
+                                           double* taubar) {
+    if (!c) return MXE_EINVAL;
+    if (!U || !V || !out) return fail(c, MXE_EINVAL, "NULL array");
+    mxe_status s = adjoint_ready(c);
+    if (s != MXE_OK) return s;
+    const size_t bytes = sizeof(double) * 14 * c->ncell;
+    const Grid2D g = adj_grid(c);
+    const dim3 pg((g.nx + 127) / 128, g.ny);
+    // U and V staged in the adjoint buffers, the result in a temporary
+    double* Up = c->adjB;
+    double* Vp = c->adjA;
+    const double* su = U;
+    const double* sv = V;
+    double* tmpU = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc(&tmpU, 2 * bytes));
+        CK(cudaMemcpyAsync(tmpU, U, bytes, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(tmpU + 14 * c->ncell, V, bytes, cudaMemcpyHostToDevice, c->stream));
+        su = tmpU;
+        sv = tmpU + 14 * c->ncell;
+    }
+    CK(cudaMemsetAsync(Up, 0, sizeof(double) * c->nelem, c->stream));
+    CK(cudaMemsetAsync(Vp, 0, sizeof(double) * c->nelem, c->stream));
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(su, Up, g, 1);
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(sv, Vp, g, 1);
+    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1), c->stream));
+    const ParamsT<double> p = make_params<double>(c->sp, c->rp);
+    double* Op = nullptr;
+    CK(cudaMalloc(&Op, sizeof(double) * c->nelem));
+    cudaError_t e = adj_stage(Up, Vp, 1.0, nullptr, nullptr, Op, c->adjP, c->adjCx, c->adjCy,
+                              c->adjG, c->adjG + 4 * GHOST_SLOTS * 14, g, p, c->stream);
+    if (e == cudaSuccess) {
+        double* dst = on_device ? out : tmpU;
+        mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && !on_device)
+            e = cudaMemcpyAsync(out, tmpU, bytes, cudaMemcpyDeviceToHost, c->stream);
+    }
+    double hg[4 * GHOST_SLOTS * 14 + 1];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hg, c->adjG, sizeof hg, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(Op);
+    cudaFree(tmpU);
+    if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint residual: %s", cudaGetErrorString(e));
+    if (gbar)
+        for (int k = 0; k < 4 * GHOST_SLOTS * 14; ++k) gbar[k] += hg[k];
+    if (taubar) *taubar += hg[4 * GHOST_SLOTS * 14];
     return MXE_OK;
 }

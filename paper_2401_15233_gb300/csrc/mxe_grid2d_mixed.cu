@@ -241,6 +241,7 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
         } else {
             a.clk->t[s1] = t + dt;
             a.clk->last_dt = dt;
+            if (a.dt_hist && a.clk->steps < a.dt_hist_cap) a.dt_hist[a.clk->steps] = dt;
             a.clk->steps += 1;
         }
     }

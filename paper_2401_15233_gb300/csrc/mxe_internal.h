@@ -57,6 +57,8 @@ struct Stage2DArgs {
     float idxf, idyf;               // 1/dx, 1/dy for the FP32 path
     int slot, final_stage;
     DevClock* clk;
+    double* dt_hist;                // optional: dt of step s at dt_hist[s] (s < dt_hist_cap)
+    long long dt_hist_cap;
 };
 
 // ---- 1D tubes ----
