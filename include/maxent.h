@@ -259,6 +259,13 @@ mxe_status mxe_adjoint_record(mxe_ctx *ctx, int n, const double *dts);
 mxe_status mxe_adjoint_run(mxe_ctx *ctx, double *ubar, int on_device, double *gbar,
                            double *taubar);
 
+/* Arithmetic of the face-state reverse in later mxe_adjoint_run /
+ * mxe_adjoint_residual calls: MXE_FP64 (default: exact linearisation, the
+ * face states recomputed and reversed in FP64) or MXE_MIXED (the face states
+ * recomputed from the FP64 tape and reversed in FP32; cell terms, the
+ * adjoint state and all accumulations stay FP64).  MXE_EINVAL otherwise. */
+mxe_status mxe_set_adjoint_precision(mxe_ctx *ctx, int precision);
+
 /* Adjoint of the residual L(U) = -div F + C at the conserved state U
  * (dense (14, ny, nx)): out = (dL/dU)^T V, and adds (dL/dg)^T V to gbar
  * and (dL/dtau_ref)^T V to *taubar.  For checking the reverse sweep one

@@ -25,7 +25,7 @@ __all__ = [
     "mxe_get_diagnostics", "mxe_last_error", "mxe_batch_create", "mxe_batch_set_relaxation",
     "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy", "mxe_tube_run_noalloc",
     "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
-    "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual",
+    "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual", "mxe_set_adjoint_precision",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, EUNREALIZABLE, ENONFINITE, ETIMEOUT, ESTATE = range(8)
@@ -111,6 +111,7 @@ def lib():
             "mxe_set_dt_history": ([_P, C.c_longlong], C.c_int),
             "mxe_get_dt_history": ([_P, C.c_longlong, _P], C.c_int),
             "mxe_adjoint_record": ([_P, C.c_int, _P], C.c_int),
+            "mxe_set_adjoint_precision": ([_P, C.c_int], C.c_int),
             "mxe_adjoint_run": ([_P, _P, C.c_int, _P, _P], C.c_int),
             "mxe_adjoint_residual": ([_P, _P, _P, _P, C.c_int, _P, _P], C.c_int),
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
@@ -274,6 +275,11 @@ def mxe_get_dt_history(ctx, n):
     return out
 
 
+def mxe_set_adjoint_precision(ctx, precision):
+    _check(ctx, lib().mxe_set_adjoint_precision(ctx, _ENUM[precision] if isinstance(precision, str)
+                                                else int(precision)))
+
+
 def mxe_adjoint_record(ctx, dts):
     d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
     _check(ctx, lib().mxe_adjoint_record(ctx, len(d), C.c_void_p(d.ctypes.data)))
@@ -386,6 +392,9 @@ class Solver:
 
     def dt_history(self, n):
         return mxe_get_dt_history(self.ctx, n)
+
+    def set_adjoint_precision(self, precision):
+        mxe_set_adjoint_precision(self.ctx, precision)
 
     def adjoint_record(self, dts):
         mxe_adjoint_record(self.ctx, dts)

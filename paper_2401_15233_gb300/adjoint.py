@@ -41,13 +41,14 @@ class JetsProblem:
     which the jets blow)."""
 
     def __init__(self, n=512, Kn=0.1, nsteps=500, ckpt=50, probe=32, mach=(3.0, 3.0),
-                 initial="developed", order=2, relax=True):
+                 initial="developed", order=2, relax=True, adjoint_precision="fp64"):
         if nsteps % ckpt:
             raise ValueError("nsteps must be a multiple of ckpt")
         if initial not in ("developed", "rest", "smooth"):
             raise ValueError("initial must be 'developed', 'rest' or 'smooth'")
         self.initial_kind = initial
         self.order, self.relax = order, relax
+        self.adjoint_precision = adjoint_precision
         self.n, self.nsteps, self.ckpt = n, nsteps, ckpt
         self.setup = wl.jets_setup(mach=mach, Kn=Kn)
         self.p0 = (float(mach[0]), float(mach[1]), float(self.setup["tau_ref"]))
@@ -67,6 +68,7 @@ class JetsProblem:
         s.set_bc(YLO, BC_DIRICHLET, lo, hi, su["bottom"])
         if self.relax:
             s.set_relaxation(TAU_HARDSPHERE, float(p[2]), su["rho_ref"], su["T_ref"])
+        s.set_adjoint_precision(self.adjoint_precision)
         return s
 
     def initial(self):

@@ -109,31 +109,31 @@ extern "C" __global__ void mxe_adj_prims(const AdjArgs a) {
 // Adjoint of the numerical flux for one of its two states (own = left if
 // isL): given both states' primal outputs and Fb, the adjoints of the own
 // state's (U, F, lmin, lmax).
-template <int K>
+template <int K, class T>
 __device__ __forceinline__ void riemann_bwd_side(const ParamsT<double>& p, bool isL,
-                                                 const double* UL, const double* FL, double lminL,
-                                                 double lmaxL, const double* UR, const double* FR,
-                                                 double lminR, double lmaxR, const double* Fb,
-                                                 double* Ub, double* Fob, double& lminb,
-                                                 double& lmaxb) {
+                                                 const T* UL, const T* FL, T lminL,
+                                                 T lmaxL, const T* UR, const T* FR,
+                                                 T lminR, T lmaxR, const T* Fb,
+                                                 T* Ub, T* Fob, T& lminb,
+                                                 T& lmaxb) {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Ub[k] = Fob[k] = 0.0;
-    lminb = lmaxb = 0.0;
+    for (int k = 0; k < NP; ++k) Ub[k] = Fob[k] = T(0.0);
+    lminb = lmaxb = T(0.0);
     if (p.flux == 1) {
-        double s = fabs(lminL);
+        T s = fabs(lminL);
         int sel = 0;
         if (fabs(lmaxL) > s) { s = fabs(lmaxL); sel = 1; }
         if (fabs(lminR) > s) { s = fabs(lminR); sel = 2; }
         if (fabs(lmaxR) > s) { s = fabs(lmaxR); sel = 3; }
-        double sb = 0.0;
+        T sb = T(0.0);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            Fob[k] = 0.5 * Fb[k];
-            Ub[k] = (isL ? 0.5 : -0.5) * s * Fb[k];
-            sb -= 0.5 * Fb[k] * (UR[k] - UL[k]);
+            Fob[k] = T(0.5) * Fb[k];
+            Ub[k] = (isL ? T(0.5) : -T(0.5)) * s * Fb[k];
+            sb -= T(0.5) * Fb[k] * (UR[k] - UL[k]);
         }
-        const double lam = sel == 0 ? lminL : sel == 1 ? lmaxL : sel == 2 ? lminR : lmaxR;
-        const double g = lam > 0.0 ? sb : (lam < 0.0 ? -sb : 0.0);
+        const T lam = sel == 0 ? lminL : sel == 1 ? lmaxL : sel == 2 ? lminR : lmaxR;
+        const T g = lam > T(0.0) ? sb : (lam < T(0.0) ? -sb : T(0.0));
         if (isL) {
             if (sel == 0) lminb = g;
             if (sel == 1) lmaxb = g;
@@ -143,27 +143,27 @@ __device__ __forceinline__ void riemann_bwd_side(const ParamsT<double>& p, bool 
         }
         return;
     }
-    const double SL = lminL < lminR ? lminL : lminR;
-    const double SR = lmaxL > lmaxR ? lmaxL : lmaxR;
-    if (SL >= 0.0) {
+    const T SL = lminL < lminR ? lminL : lminR;
+    const T SR = lmaxL > lmaxR ? lmaxL : lmaxR;
+    if (SL >= T(0.0)) {
         if (isL)
 #pragma unroll
             for (int k = 0; k < NP; ++k) Fob[k] = Fb[k];
         return;
     }
-    if (SR <= 0.0) {
+    if (SR <= T(0.0)) {
         if (!isL)
 #pragma unroll
             for (int k = 0; k < NP; ++k) Fob[k] = Fb[k];
         return;
     }
-    const double inv = 1.0 / (SR - SL);
-    const double SLR = SL * SR;
-    double SRb = 0.0, SLb = 0.0;
+    const T inv = T(1.0) / (SR - SL);
+    const T SLR = SL * SR;
+    T SRb = T(0.0), SLb = T(0.0);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        const double dU = UR[k] - UL[k];
-        const double F = (SR * FL[k] - SL * FR[k] + SLR * dU) * inv;
+        const T dU = UR[k] - UL[k];
+        const T F = (SR * FL[k] - SL * FR[k] + SLR * dU) * inv;
         Fob[k] = isL ? Fb[k] * SR * inv : -Fb[k] * SL * inv;
         Ub[k] = isL ? -Fb[k] * SLR * inv : Fb[k] * SLR * inv;
         SRb += Fb[k] * (FL[k] + SL * dU - F) * inv;
@@ -174,35 +174,52 @@ __device__ __forceinline__ void riemann_bwd_side(const ParamsT<double>& p, bool 
     if (isL == selL_max) lmaxb = SRb;
 }
 
-__device__ __forceinline__ double shfl1(double v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl1(double v, unsigned m = 0xffffffffu) {
+    return __shfl_xor_sync(m, v, 1);
+}
+__device__ __forceinline__ float shfl1(float v, unsigned m = 0xffffffffu) {
+    return __shfl_xor_sync(m, v, 1);
+}
 
 // One face state per thread, two threads (adjacent lanes) per face: lane
 // parity 0 = left state (cell f-1, stencil f-2..f), 1 = right state (cell f,
 // stencil f-1..f+1).  f in [0, n_K] on line t (row j for x-faces, column i
 // for y-faces).  Threads past the last face compute the last face (the
 // shuffles need the whole warp) and write nothing.
-template <int K>
+template <int K, class T>
 __device__ __forceinline__ void adj_face_side(const AdjArgs& a, int f, int t, bool valid) {
     const Grid2D& g = a.g;
     const ParamsT<double>& p = a.p;
     const int nK = K == 0 ? g.nx : g.ny;
     const bool isL = (threadIdx.x & 1) == 0;
     const int c0 = isL ? f - 1 : f;                      // own cell
-    double Qs[3][NP];
+    // reconstruction and limiter in FP64 (differences of nearby states); the
+    // face state itself in T.  The stencil is loaded again for the
+    // reconstruction reverse rather than kept live through the face state.
+    auto load_stencil = [&](double (*Qs)[NP]) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        if (K == 0) stencil_prim(a, c0 - 1 + m, t, Qs[m]);
-        else stencil_prim(a, t, c0 - 1 + m, Qs[m]);
-    }
-    adj::PhiAdj ph{0.0, 0.0, 0.0, -1};
-    if (p.order == 2) ph = adj::phi_adj<NP>(Qs[0], Qs[1], Qs[2], p.limiter);
+        for (int m = 0; m < 3; ++m) {
+            if (K == 0) stencil_prim(a, c0 - 1 + m, t, Qs[m]);
+            else stencil_prim(a, t, c0 - 1 + m, Qs[m]);
+        }
+    };
+    adj::PhiAdj<double> ph{0.0, 0.0, 0.0, -1};
     const double hs = isL ? 0.5 : -0.5;
-    double Qf[NP];
+    T Qf[NP];
+    {
+        double Qs[3][NP];
+        load_stencil(Qs);
+        if (p.order == 2) ph = adj::phi_adj<double, NP>(Qs[0], Qs[1], Qs[2], p.limiter);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Qf[k] = muscl_face(Qs[0][k], Qs[1][k], Qs[2][k], ph.phi, hs);
+        for (int k = 0; k < NP; ++k)
+            Qf[k] = (T)muscl_face(Qs[0][k], Qs[1][k], Qs[2][k], ph.phi, hs);
+    }
     // adjoint of the face flux: L_l -= F idx, L_r += F idx
     const double idx = K == 0 ? g.idx : g.idy;
-    double Fb[NP];
+    // The reverse is linear in the flux adjoint: it runs on Fb scaled by a
+    // power of two (so that FP32 cannot overflow) and the result is scaled
+    // back.  A face whose flux adjoint is zero contributes nothing.
+    double Fbd[NP];
     {
         const int l = f - 1, r = f;
         const long long ol = K == 0 ? (long long)t * g.pitch + l : (long long)l * g.pitch + t;
@@ -212,38 +229,54 @@ __device__ __forceinline__ void adj_face_side(const AdjArgs& a, int f, int t, bo
             const long long fo = planar_field(k) * g.fstride;
             const double vl = l >= 0 ? a.V[ol + fo] : 0.0;
             const double vr = r < nK ? a.V[orr + fo] : 0.0;
-            Fb[k] = ((vr - vl) * a.coef) * idx;
+            Fbd[k] = ((vr - vl) * a.coef) * idx;
         }
     }
-    double Qb[NP];
+    double fmax = 0.0;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Qb[k] = 0.0;
-    auto outadj = [&](const double* U, const double* F, double lmin, double lmax, double* Ub,
-                      double* Fob, double& lminb, double& lmaxb) {
-        double Up[NP], Fp[NP];
+    for (int k = 0; k < NP; ++k) fmax = fmax > fabs(Fbd[k]) ? fmax : fabs(Fbd[k]);
+    const bool live = fmax > 0.0;                       // same in both lanes of the face
+    const unsigned mask = __ballot_sync(0xffffffffu, live);
+    int ex = 0;
+    if (live) frexp(fmax, &ex);
+    const double scale = ldexp(1.0, ex);
+    T Fb[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Fb[k] = (T)(Fbd[k] / scale);
+    T Qb[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Qb[k] = T(0);
+    auto outadj = [&](const T* U, const T* F, T lmin, T lmax, T* Ub, T* Fob, T& lminb,
+                      T& lmaxb) {
+        T Up[NP], Fp[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            Up[k] = shfl1(U[k]);
-            Fp[k] = shfl1(F[k]);
+            Up[k] = shfl1(U[k], mask);
+            Fp[k] = shfl1(F[k], mask);
         }
-        const double lminp = shfl1(lmin), lmaxp = shfl1(lmax);
+        const T lminp = shfl1(lmin, mask), lmaxp = shfl1(lmax, mask);
         if (isL)
-            riemann_bwd_side<K>(p, true, U, F, lmin, lmax, Up, Fp, lminp, lmaxp, Fb, Ub, Fob,
+            riemann_bwd_side<K, T>(p, true, U, F, lmin, lmax, Up, Fp, lminp, lmaxp, Fb, Ub, Fob,
                                 lminb, lmaxb);
         else
-            riemann_bwd_side<K>(p, false, Up, Fp, lminp, lmaxp, U, F, lmin, lmax, Fb, Ub, Fob,
+            riemann_bwd_side<K, T>(p, false, Up, Fp, lminp, lmaxp, U, F, lmin, lmax, Fb, Ub, Fob,
                                 lminb, lmaxb);
     };
-    adj::face_side_adj<K>(Qf, p.sigma_lim, p.k_ws, outadj, Qb);
+    if (live) adj::face_side_adj<T, K>(Qf, (T)p.sigma_lim, (T)p.k_ws, outadj, Qb);
     // reconstruction reverse -> own stencil (bm, b0, bp)
-    double bm[NP], b0[NP], bp[NP];
+    double Qbd[NP], bm[NP], b0[NP], bp[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) bm[k] = b0[k] = bp[k] = 0.0;
+    for (int k = 0; k < NP; ++k) {
+        Qbd[k] = (double)Qb[k] * scale;
+        bm[k] = b0[k] = bp[k] = 0.0;
+    }
     if (p.order == 2) {
-        adj::muscl_bwd<NP>(Qs[0], Qs[1], Qs[2], ph, hs, Qb, bm, b0, bp);
+        double Qs[3][NP];
+        load_stencil(Qs);
+        adj::muscl_bwd<double, NP>(Qs[0], Qs[1], Qs[2], ph, hs, Qbd, bm, b0, bp);
     } else {
 #pragma unroll
-        for (int k = 0; k < NP; ++k) b0[k] = Qb[k];
+        for (int k = 0; k < NP; ++k) b0[k] = Qbd[k];
     }
     // slots of the face: 0 = f-2, 1 = f-1, 2 = f, 3 = f+1.  Left state: bm,
     // b0, bp -> slots 0, 1, 2; right state: slots 1, 2, 3.  Exchange the
@@ -267,16 +300,24 @@ __device__ __forceinline__ void adj_face_side(const AdjArgs& a, int f, int t, bo
 }
 
 // 128 threads = 64 faces of one line (x) or 64 columns of one face row (y)
-extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_x(const AdjArgs a) {
+template <class T>
+__device__ __forceinline__ void faces_x(const AdjArgs& a) {
     const int f = blockIdx.x * 64 + (threadIdx.x >> 1), j = blockIdx.y;
     const bool valid = f <= a.g.nx;
-    adj_face_side<0>(a, valid ? f : a.g.nx, j, valid);
+    adj_face_side<0, T>(a, valid ? f : a.g.nx, j, valid);
 }
-extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_y(const AdjArgs a) {
+template <class T>
+__device__ __forceinline__ void faces_y(const AdjArgs& a) {
     const int i = blockIdx.x * 64 + (threadIdx.x >> 1), f = blockIdx.y;
     const bool valid = i < a.g.nx;
-    adj_face_side<1>(a, f, valid ? i : a.g.nx - 1, valid);
+    adj_face_side<1, T>(a, f, valid ? i : a.g.nx - 1, valid);
 }
+// FP64 reverse (exact linearisation) and FP32 reverse (the face states
+// recomputed and reversed in FP32 from the FP64 states of the tape)
+extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_x(const AdjArgs a) { faces_x<double>(a); }
+extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_y(const AdjArgs a) { faces_y<double>(a); }
+extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_x_f32(const AdjArgs a) { faces_x<float>(a); }
+extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_y_f32(const AdjArgs a) { faces_y<float>(a); }
 
 // Sum of the x-face contributions to stencil position (v, j): slot s of face
 // f targets cell f - 2 + s.
@@ -432,15 +473,20 @@ size_t adj_args_size() { return sizeof(AdjArgs); }
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      cudaStream_t st) {
+                      bool f32, cudaStream_t st) {
     AdjArgs a;
     a.U = U; a.V = V; a.coef = coef; a.b1 = b1; a.b2 = b2; a.out = out;
     a.P = P; a.Cx = Cx; a.Cy = Cy; a.gbar = gbar; a.taubar = taubar;
     a.g = g; a.p = p;
     dim3 cg((g.nx + 127) / 128, g.ny);
     mxe_adj_prims<<<cg, 128, 0, st>>>(a);
-    mxe_adj_faces_x<<<dim3((g.nx + 1 + 63) / 64, g.ny), 128, 0, st>>>(a);
-    mxe_adj_faces_y<<<dim3((g.nx + 63) / 64, g.ny + 1), 128, 0, st>>>(a);
+    if (f32) {
+        mxe_adj_faces_x_f32<<<dim3((g.nx + 1 + 63) / 64, g.ny), 128, 0, st>>>(a);
+        mxe_adj_faces_y_f32<<<dim3((g.nx + 63) / 64, g.ny + 1), 128, 0, st>>>(a);
+    } else {
+        mxe_adj_faces_x<<<dim3((g.nx + 1 + 63) / 64, g.ny), 128, 0, st>>>(a);
+        mxe_adj_faces_y<<<dim3((g.nx + 63) / 64, g.ny + 1), 128, 0, st>>>(a);
+    }
     mxe_adj_ghosts<<<(4 * (g.nx + g.ny) + 127) / 128, 128, 0, st>>>(a);
     mxe_adj_cells<<<cg, 128, 0, st>>>(a);
     return cudaGetLastError();

@@ -47,7 +47,7 @@ const void* tubes_mixed_kernel(bool planar, int nt);
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      cudaStream_t st);
+                      bool f32, cudaStream_t st);
 extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g,
                                         int to_pitched);
 size_t tubes_mixed_smem(bool planar, int nt);
@@ -110,6 +110,7 @@ struct mxe_ctx {
     double* adjA = nullptr;           // adjoint state buffers (pitched)
     double* adjB = nullptr;
     double* adjG = nullptr;           // [4][GHOST_SLOTS][14] imposed-state adjoint, then tau_ref's
+    bool adj_f32 = false;             // face-state reverse in FP32 (MXE_MIXED adjoint)
     // state
     double* U = nullptr;
     double* Us = nullptr;
@@ -1294,14 +1295,14 @@ extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, d
         if (rk2) {
             // U^{n+1} = U^n + dt L(U*): B = dt L'(U*)^T A
             e = adj_stage(un + c->nelem, c->adjA, dt, nullptr, nullptr, c->adjB, c->adjP,
-                          c->adjCx, c->adjCy, gb, tb, g, p, c->stream);
+                          c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
             // U* = U^n + dt/2 L(U^n): A = A + B + dt/2 L'(U^n)^T B
             if (e == cudaSuccess)
                 e = adj_stage(un, c->adjB, 0.5 * dt, c->adjA, c->adjB, c->adjA, c->adjP,
-                              c->adjCx, c->adjCy, gb, tb, g, p, c->stream);
+                              c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
         } else {
             e = adj_stage(un, c->adjA, dt, c->adjA, nullptr, c->adjA, c->adjP, c->adjCx,
-                          c->adjCy, gb, tb, g, p, c->stream);
+                          c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
         }
         if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint stage: %s", cudaGetErrorString(e));
     }
@@ -1351,7 +1352,8 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
     double* Op = nullptr;
     CK(cudaMalloc(&Op, sizeof(double) * c->nelem));
     cudaError_t e = adj_stage(Up, Vp, 1.0, nullptr, nullptr, Op, c->adjP, c->adjCx, c->adjCy,
-                              c->adjG, c->adjG + 4 * GHOST_SLOTS * 14, g, p, c->stream);
+                              c->adjG, c->adjG + 4 * GHOST_SLOTS * 14, g, p, c->adj_f32,
+                              c->stream);
     if (e == cudaSuccess) {
         double* dst = on_device ? out : tmpU;
         mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0);
@@ -1369,5 +1371,13 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
     if (gbar)
         for (int k = 0; k < 4 * GHOST_SLOTS * 14; ++k) gbar[k] += hg[k];
     if (taubar) *taubar += hg[4 * GHOST_SLOTS * 14];
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_adjoint_precision(mxe_ctx* c, int precision) {
+    if (!c) return MXE_EINVAL;
+    if (precision != MXE_FP64 && precision != MXE_MIXED)
+        return fail(c, MXE_EINVAL, "precision must be MXE_FP64 or MXE_MIXED");
+    c->adj_f32 = precision == MXE_MIXED;
     return MXE_OK;
 }

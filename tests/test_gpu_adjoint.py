@@ -105,8 +105,9 @@ def test_adjoint_steps_dot_product(mx, orc, smooth):
         assert abs(lhs - rhs) <= 1e-8 * (abs(lhs) + 1e-300), (name, lhs, rhs)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("initial", ["rest", "smooth"])
-def test_adjoint_probe_gradient_vs_fd(mx, initial):
+def test_adjoint_probe_gradient_vs_fd(mx, initial, precision):
     """Crossed jets (64^2, 200 RK2 steps, checkpoints every 40): gradient of
     the probe-mean density w.r.t. both Mach numbers and tau_ref against
     central differences of the frozen-dt map.  First-order reconstruction:
@@ -114,9 +115,11 @@ def test_adjoint_probe_gradient_vs_fd(mx, initial):
     differentiable at the scale of any finite difference (the limiter ratio
     of fields whose differences are near round-off makes finite differences
     diverge as h -> 0); there the adjoint is checked against the oracle's
-    tangent instead (test_adjoint_steps_dot_product)."""
+    tangent instead (test_adjoint_steps_dot_product).  precision "mixed":
+    the face states reversed in FP32 from the FP64 tape."""
     from paper_2401_15233_gb300 import adjoint as ad
-    prob = ad.JetsProblem(n=64, nsteps=200, ckpt=40, probe=8, initial=initial, order=1)
+    prob = ad.JetsProblem(n=64, nsteps=200, ckpt=40, probe=8, initial=initial, order=1,
+                          adjoint_precision=precision)
     p0 = prob.params0()
     J, ckpts, dts, s = ad.forward_checkpointed(prob, p0)
     g, _ = ad.backward_checkpointed(prob, s, ckpts, dts)
@@ -128,7 +131,7 @@ def test_adjoint_probe_gradient_vs_fd(mx, initial):
         e[k] = hs[k]
         fd.append((ad.run_fixed(prob, p0 + e, dts) - ad.run_fixed(prob, p0 - e, dts)) / (2 * hs[k]))
     fd = np.array(fd)
-    print(f"{initial}: probe J {J:.10e} adjoint {g} fd {fd}")
+    print(f"{initial} {precision}: probe J {J:.10e} adjoint {g} fd {fd}")
     assert np.all(np.abs(fd) > 0)
     assert np.all(np.abs(g - fd) <= 1e-4 * np.abs(fd)), (g, fd)
 
@@ -144,3 +147,33 @@ def test_adjoint_autograd_function(mx):
     g, _ = ad.backward_checkpointed(prob, s, ckpts, dts)
     assert float(J) == Jd
     assert np.allclose(p.grad.numpy(), g, rtol=1e-12, atol=0)
+
+
+def test_adjoint_mixed_matches_fp64(mx, orc):
+    """FP32 face-state reverse against the FP64 one on the MUSCL jets steps of
+    the dot-product test: same adjoint up to FP32 rounding."""
+    n = 20
+    setup, U, rng = case(orc, n, 2, True)
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    dts = []
+    X = U
+    for _ in range(5):
+        dts.append(orc.dt(cfg, X, 0.0, 10.0))
+        X = orc.step(cfg, X, dts[-1])
+    ybar = rng.standard_normal(U.shape)
+    ybar[..., Z_ODD] = 0.0
+    res = {}
+    for prec in ("fp64", "mixed"):
+        s = jets_gpu_solver(mx, n, n, setup)
+        s.set_adjoint_precision(prec)
+        s.set_state(aos_to_soa(U), kind="conserved")
+        s.adjoint_record(dts)
+        xbar = aos_to_soa(ybar.copy())
+        gb, tb = s.adjoint_run(xbar)
+        res[prec] = (xbar, gb, tb)
+    a, b = res["fp64"], res["mixed"]
+    e = np.linalg.norm(a[0] - b[0]) / np.linalg.norm(a[0])
+    eg = np.linalg.norm(a[1] - b[1]) / np.linalg.norm(a[1])
+    et = abs(a[2] - b[2]) / abs(a[2])
+    print(f"mixed vs fp64 adjoint: state {e:.2e} inflow {eg:.2e} tau {et:.2e}")
+    assert e < 1e-4 and eg < 1e-4 and et < 1e-4
