@@ -61,7 +61,26 @@ def parse():
                    help="skip the batched-tube leg (256 Sod tubes, one graph launch)")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint leg (512^2 crossed jets, 500 steps, checkpoints every 50)")
+    p.add_argument("--only", default=None, choices=["batch", "adjoint"],
+                   help="run one secondary leg alone (profiling runs)")
+    p.add_argument("--batch-t-end", type=float, default=0.2)
+    p.add_argument("--adj-n", type=int, default=512)
+    p.add_argument("--adj-steps", type=int, default=500)
+    p.add_argument("--adj-ckpt", type=int, default=50)
+    p.add_argument("--adj-precision", default=None, choices=["fp64", "mixed"],
+                   help="--only adjoint: one reverse precision, no finite differences")
     return p.parse_args()
+
+
+def finite_json(x):
+    """Non-finite floats -> null (strict JSON)."""
+    if isinstance(x, float):
+        return x if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: finite_json(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [finite_json(v) for v in x]
+    return x
 
 
 def peaks():
@@ -181,7 +200,7 @@ def cpu_baseline(wl, seconds_target=15.0):
             "sample": f"{n}x{n} crossed jets, {steps} RK2 steps incl. CFL, {el:.1f} s, 1 thread"}
 
 
-def bench_batch(mx, wl, stream, world):
+def bench_batch(mx, wl, stream, world, t_end=0.2):
     """Batched 14-moment Sod tubes: 256 tubes of 512..8192 cells, Kn in
     [1e-3, 10], density ratio in [4, 20], each run to t = 0.2 in one persistent
     launch replayed from a CUDA graph, block shape from the autotuner.  Also
@@ -215,9 +234,9 @@ def bench_batch(mx, wl, stream, world):
 
     b = make("mixed")
     nt, cl, tune_ms = b.autotune(0.002)
-    b.run(10 ** 8, 0.2)                   # warm-up: captures the graph for t_end = 0.2
+    b.run(10 ** 8, t_end)                 # warm-up: captures the graph for t_end
     b.set_state(b.pack(prims))            # back to t = 0 (same launch arguments: replay)
-    ms, cu, st = timed_run(b, 0.2)
+    ms, cu, st = timed_run(b, t_end)
     d = b.diagnostics()
     bw = make("mixed")
     bw.set_shape(nt, cl)
@@ -246,7 +265,7 @@ def bench_batch(mx, wl, stream, world):
     }
 
 
-def bench_adjoint(world):
+def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
     """Discrete adjoint of the crossed jets, 512^2, Kn = 0.1, 500 RK2 steps
     from the background at rest, checkpoints every 50 steps: gradient of the
     mean density over the central 32 x 32 probe w.r.t. both Mach numbers and
@@ -258,12 +277,12 @@ def bench_adjoint(world):
     import numpy as np
     import torch
     from paper_2401_15233_gb300 import adjoint as ad
-    out = {"workload": "crossed jets 512x512, Kn 0.1, 500 RK2 steps from rest, checkpoints "
-                       "every 50, probe 32x32 at the centre; FP64"}
+    out = {"workload": f"crossed jets {n}x{n}, Kn 0.1, {nsteps} RK2 steps from rest, "
+                       f"checkpoints every {ckpt}, probe 32x32 at the centre; FP64 forward"}
     w = ad.JetsProblem(n=64, nsteps=20, ckpt=10, probe=8, initial="rest")
     Jw, c, d, sw = ad.forward_checkpointed(w, w.params0())      # warm-up
     ad.backward_checkpointed(w, sw, c, d)
-    prob = ad.JetsProblem(n=512, nsteps=500, ckpt=50, probe=32, initial="rest", order=2)
+    prob = ad.JetsProblem(n=n, nsteps=nsteps, ckpt=ckpt, probe=32, initial="rest", order=2)
     p0 = prob.params0()
     s = prob.solver(p0)
     s.set_state(prob.initial())
@@ -274,7 +293,7 @@ def bench_adjoint(world):
     tf = time.perf_counter() - t0
     del s
     out["forward_s"] = tf
-    for prec in ("fp64", "mixed"):
+    for prec in ((only_precision,) if only_precision else ("fp64", "mixed")):
         prob.adjoint_precision = prec
         t0 = time.perf_counter()
         J, ckpts, dts, s2 = ad.forward_checkpointed(prob, p0)
@@ -287,13 +306,16 @@ def bench_adjoint(world):
         out[prec] = {"forward_ckpt_s": tfc, "backward_s": tb, "ratio": (tfc + tb) / tf,
                      "grad": [float(x) for x in g]}
         del s2, ckpts
+    out.update({"t_final": float(dts.sum()), "J": J,
+                "probe_at_background": bool(J == prob.setup["background"][0])})
+    if only_precision:
+        return out
     fd = []
     for k in range(3):
         e = np.zeros(3)
         e[k] = 1e-4 * (p0[2] if k == 2 else 1.0)
         fd.append((ad.run_fixed(prob, p0 + e, dts) - ad.run_fixed(prob, p0 - e, dts)) / (2 * e[k]))
-    out.update({"t_final": float(dts.sum()), "J": J, "fd": [float(x) for x in fd],
-                "probe_at_background": bool(J == prob.setup["background"][0])})
+    out["fd"] = [float(x) for x in fd]
     out["ratio"] = out["fp64"]["ratio"]
     return out
 
@@ -344,6 +366,16 @@ def main():
     world, rank, local, dist = dist_setup(args)
     torch.cuda.set_device(local)
     import paper_2401_15233_gb300 as mx
+    if args.only:
+        stream = torch.cuda.Stream()
+        if args.only == "batch":
+            leg = bench_batch(mx, wl, stream, world, args.batch_t_end)
+        else:
+            leg = bench_adjoint(world, args.adj_n, args.adj_steps, args.adj_ckpt,
+                                args.adj_precision)
+        if rank == 0:
+            print(json.dumps(finite_json({"only": args.only, args.only: leg})), flush=True)
+        return
 
     n = args.n
     setup = wl.jets_setup(Kn=0.1)
@@ -449,12 +481,12 @@ def main():
                  if d["n_closures"] else None},
     }
     if not args.no_batch:
-        out["batch"] = bench_batch(mx, wl, stream, world)
+        out["batch"] = bench_batch(mx, wl, stream, world, args.batch_t_end)
     if not args.no_adjoint:
         out["adjoint"] = bench_adjoint(world)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl)
-    print(json.dumps(out), flush=True)
+    print(json.dumps(finite_json(out)), flush=True)
 
 
 if __name__ == "__main__":

@@ -37,6 +37,15 @@ struct AdjArgs {
     double* gbar;               // [4][GHOST_SLOTS][14] adjoint of imposed states (accumulated)
     double* taubar;             // adjoint of tau_ref (accumulated)
     double coef;                // c dt of the stage: V is scaled by it
+    // FP32 face-state reverse: per-cell data formed once in FP64
+    float* Pf;                  // [NP][ny][pitch] primitives
+    float* Vf;                  // [NP][ny][pitch] coef * V
+    float* DX;                  // [NP][ny][nx+3] Q(i+1) - Q(i), i = -2 .. nx (ghosts included)
+    float* DY;                  // [NP][ny+3][nx] Q(j+1) - Q(j), j = -2 .. ny
+    float* LX;                  // [4][ny][nx+2] x limiter of cell i = -1 .. nx (phi, dphi/ddm,
+                                //   dphi/ddp, selected field), formed in FP64
+    float* LY;                  // [4][ny+2][nx] y limiter of cell j = -1 .. ny
+    int f32;                    // contributions Cx, Cy stored as float
     Grid2D g;
     ParamsT<double> p;
 };
@@ -104,6 +113,83 @@ extern "C" __global__ void mxe_adj_prims(const AdjArgs a) {
     cons2prim_p_rn(Uc, Q);
 #pragma unroll
     for (int k = 0; k < NP; ++k) a.P[o + k * g.fstride] = Q[k];
+    if (a.f32) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            a.Pf[o + k * g.fstride] = (float)Q[k];
+            a.Vf[o + k * g.fstride] = (float)(a.coef * a.V[o + planar_field(k) * g.fstride]);
+        }
+    }
+}
+
+// FP32 path: stencil differences in FP64, stored in FP32 (their own
+// relative precision, not that of the states), ghost cells included.
+__device__ __forceinline__ long long dx_index(const Grid2D& g, int k, int j, int i) {
+    return ((long long)k * g.ny + j) * (g.nx + 3) + (i + 2);
+}
+__device__ __forceinline__ long long dy_index(const Grid2D& g, int k, int j, int i) {
+    return ((long long)k * (g.ny + 3) + (j + 2)) * g.nx + i;
+}
+__device__ __forceinline__ long long lx_index(const Grid2D& g, int m, int j, int i) {
+    return ((long long)m * g.ny + j) * (g.nx + 2) + (i + 1);
+}
+__device__ __forceinline__ long long ly_index(const Grid2D& g, int m, int j, int i) {
+    return ((long long)m * (g.ny + 2) + (j + 1)) * g.nx + i;
+}
+
+// The shared limiter of every cell and direction (ghost cells next to the
+// boundary included) in FP64, so that the FP32 reverse takes the FP64
+// branches: phi, its derivatives and the field that sets it.
+extern "C" __global__ void mxe_adj_limiters(const AdjArgs a) {
+    const Grid2D& g = a.g;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxc = (g.nx + 2) * g.ny, nyc = g.nx * (g.ny + 2);
+    int i, j, K;
+    if (id < nxc) {
+        j = id / (g.nx + 2);
+        i = id % (g.nx + 2) - 1;
+        K = 0;
+    } else if (id < nxc + nyc) {
+        const int r = id - nxc;
+        i = r % g.nx;
+        j = r / g.nx - 1;
+        K = 1;
+    } else {
+        return;
+    }
+    double qm[NP], q0[NP], qp[NP];
+    stencil_prim(a, K == 0 ? i - 1 : i, K == 0 ? j : j - 1, qm);
+    stencil_prim(a, i, j, q0);
+    stencil_prim(a, K == 0 ? i + 1 : i, K == 0 ? j : j + 1, qp);
+    adj::PhiAdj<double> ph{1.0, 0.0, 0.0, -1};
+    if (a.p.order == 2) ph = adj::phi_adj<double, NP>(qm, q0, qp, a.p.limiter);
+    else ph.phi = 0.0;
+    float* L = K == 0 ? a.LX : a.LY;
+    const float v[4] = {(float)ph.phi, (float)ph.ddm, (float)ph.ddp, (float)ph.ks};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) L[K == 0 ? lx_index(g, m, j, i) : ly_index(g, m, j, i)] = v[m];
+}
+
+extern "C" __global__ void mxe_adj_diffs(const AdjArgs a) {
+    const Grid2D& g = a.g;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxp = (g.nx + 3) * g.ny, nyp = g.nx * (g.ny + 3);
+    if (id < nxp) {                                  // x pairs (i, i+1) of row j
+        const int j = id / (g.nx + 3), i = id % (g.nx + 3) - 2;
+        double q0[NP], q1[NP];
+        stencil_prim(a, i, j, q0);
+        stencil_prim(a, i + 1, j, q1);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) a.DX[dx_index(g, k, j, i)] = (float)(q1[k] - q0[k]);
+    } else if (id < nxp + nyp) {                     // y pairs (j, j+1) of column i
+        const int r = id - nxp;
+        const int i = r % g.nx, j = r / g.nx - 2;
+        double q0[NP], q1[NP];
+        stencil_prim(a, i, j, q0);
+        stencil_prim(a, i, j + 1, q1);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) a.DY[dy_index(g, k, j, i)] = (float)(q1[k] - q0[k]);
+    }
 }
 
 // Adjoint of the numerical flux for one of its two states (own = left if
@@ -299,21 +385,142 @@ __device__ __forceinline__ void adj_face_side(const AdjArgs& a, int f, int t, bo
     }
 }
 
+// FP32 variant: everything from the per-cell FP32 data (primitives, the
+// FP64-formed stencil differences, coef * V), no FP64 arithmetic except for
+// the own cell of a boundary face that is a ghost cell.  Contributions are
+// stored as float.
+template <int K>
+__device__ __forceinline__ void adj_face_side_f32(const AdjArgs& a, int f, int t, bool valid) {
+    const Grid2D& g = a.g;
+    const ParamsT<double>& p = a.p;
+    const int nK = K == 0 ? g.nx : g.ny;
+    const bool isL = (threadIdx.x & 1) == 0;
+    const int c0 = isL ? f - 1 : f;                      // own cell
+    float dm[NP], dp[NP], Qf[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        dm[k] = K == 0 ? a.DX[dx_index(g, k, t, c0 - 1)] : a.DY[dy_index(g, k, c0 - 1, t)];
+        dp[k] = K == 0 ? a.DX[dx_index(g, k, t, c0)] : a.DY[dy_index(g, k, c0, t)];
+    }
+    if (c0 >= 0 && c0 < nK) {
+        const long long o = K == 0 ? (long long)t * g.pitch + c0 : (long long)c0 * g.pitch + t;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) Qf[k] = a.Pf[o + k * g.fstride];
+    } else {
+        double Qd[NP];
+        if (K == 0) stencil_prim(a, c0, t, Qd);
+        else stencil_prim(a, t, c0, Qd);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) Qf[k] = (float)Qd[k];
+    }
+    adj::PhiAdj<float> ph;
+    {
+        const float* L = K == 0 ? a.LX : a.LY;
+        auto at = [&](int m) {
+            return L[K == 0 ? lx_index(g, m, t, c0) : ly_index(g, m, c0, t)];
+        };
+        ph.phi = at(0);
+        ph.ddm = at(1);
+        ph.ddp = at(2);
+        ph.ks = (int)at(3);
+    }
+    const float hs = isL ? 0.5f : -0.5f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Qf[k] = Qf[k] + hs * (ph.phi * (0.5f * (dm[k] + dp[k])));
+    // flux adjoint from coef * V (0 at ghost cells), scaled by a power of two
+    const float idx = (float)(K == 0 ? g.idx : g.idy);
+    float Fb[NP];
+    {
+        const int l = f - 1, r = f;
+        const long long ol = K == 0 ? (long long)t * g.pitch + l : (long long)l * g.pitch + t;
+        const long long orr = K == 0 ? (long long)t * g.pitch + r : (long long)r * g.pitch + t;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float vl = l >= 0 ? a.Vf[ol + k * g.fstride] : 0.0f;
+            const float vr = r < nK ? a.Vf[orr + k * g.fstride] : 0.0f;
+            Fb[k] = (vr - vl) * idx;
+        }
+    }
+    float fmax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) fmax = fmaxf(fmax, fabsf(Fb[k]));
+    const bool live = fmax > 0.0f;
+    const unsigned mask = __ballot_sync(0xffffffffu, live);
+    int ex = 0;
+    if (live) frexpf(fmax, &ex);
+    // exponent shifts (a power-of-two factor 2^-ex itself can overflow FP32
+    // when the adjoint is still tiny, i.e. subnormal, at the edge of its support)
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Fb[k] = ldexpf(Fb[k], -ex);
+    float Qb[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Qb[k] = 0.0f;
+    auto outadj = [&](const float* U, const float* F, float lmin, float lmax, float* Ub,
+                      float* Fob, float& lminb, float& lmaxb) {
+        float Up[NP], Fp[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            Up[k] = shfl1(U[k], mask);
+            Fp[k] = shfl1(F[k], mask);
+        }
+        const float lminp = shfl1(lmin, mask), lmaxp = shfl1(lmax, mask);
+        if (isL)
+            riemann_bwd_side<K, float>(p, true, U, F, lmin, lmax, Up, Fp, lminp, lmaxp, Fb, Ub,
+                                       Fob, lminb, lmaxb);
+        else
+            riemann_bwd_side<K, float>(p, false, Up, Fp, lminp, lmaxp, U, F, lmin, lmax, Fb, Ub,
+                                       Fob, lminb, lmaxb);
+    };
+    if (live)
+        adj::face_side_adj<float, K>(Qf, (float)p.sigma_lim, (float)p.k_ws, outadj, Qb);
+    float bm[NP], b0[NP], bp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        Qb[k] = ldexpf(Qb[k], ex);
+        bm[k] = b0[k] = bp[k] = 0.0f;
+    }
+    if (p.order == 2) {
+        adj::muscl_bwd_d<float, NP>(dm, dp, ph, hs, Qb, bm, b0, bp);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) b0[k] = Qb[k];
+    }
+    float* Cf = reinterpret_cast<float*>(K == 0 ? a.Cx : a.Cy);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float send = isL ? bp[k] : bm[k];
+        const float recv = shfl1(send);
+        if (!valid) continue;
+        const float lo = isL ? bm[k] : b0[k] + recv;
+        const float hi = isL ? b0[k] + recv : bp[k];
+        const int s0 = isL ? 0 : 2;
+        if (K == 0) {
+            Cf[cx_index(g, s0, k, t, f)] = lo;
+            Cf[cx_index(g, s0 + 1, k, t, f)] = hi;
+        } else {
+            Cf[cy_index(g, s0, k, f, t)] = lo;
+            Cf[cy_index(g, s0 + 1, k, f, t)] = hi;
+        }
+    }
+}
+
 // 128 threads = 64 faces of one line (x) or 64 columns of one face row (y)
 template <class T>
 __device__ __forceinline__ void faces_x(const AdjArgs& a) {
     const int f = blockIdx.x * 64 + (threadIdx.x >> 1), j = blockIdx.y;
     const bool valid = f <= a.g.nx;
-    adj_face_side<0, T>(a, valid ? f : a.g.nx, j, valid);
+    if (sizeof(T) == 4) adj_face_side_f32<0>(a, valid ? f : a.g.nx, j, valid);
+    else adj_face_side<0, T>(a, valid ? f : a.g.nx, j, valid);
 }
 template <class T>
 __device__ __forceinline__ void faces_y(const AdjArgs& a) {
     const int i = blockIdx.x * 64 + (threadIdx.x >> 1), f = blockIdx.y;
     const bool valid = i < a.g.nx;
-    adj_face_side<1, T>(a, f, valid ? i : a.g.nx - 1, valid);
+    if (sizeof(T) == 4) adj_face_side_f32<1>(a, f, valid ? i : a.g.nx - 1, valid);
+    else adj_face_side<1, T>(a, f, valid ? i : a.g.nx - 1, valid);
 }
 // FP64 reverse (exact linearisation) and FP32 reverse (the face states
-// recomputed and reversed in FP32 from the FP64 states of the tape)
+// recomputed and reversed in FP32 from per-cell FP32 data)
 extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_x(const AdjArgs a) { faces_x<double>(a); }
 extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_y(const AdjArgs a) { faces_y<double>(a); }
 extern "C" __global__ void __launch_bounds__(128) mxe_adj_faces_x_f32(const AdjArgs a) { faces_x<float>(a); }
@@ -327,8 +534,10 @@ __device__ __forceinline__ void gather_x(const AdjArgs& a, int v, int j, double*
     for (int s = 0; s < 4; ++s) {
         const int f = v + 2 - s;
         if (f < 0 || f > g.nx) continue;
+        const float* cf = reinterpret_cast<const float*>(a.Cx);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) Qb[k] += a.Cx[cx_index(g, s, k, j, f)];
+        for (int k = 0; k < NP; ++k)
+            Qb[k] += a.f32 ? (double)cf[cx_index(g, s, k, j, f)] : a.Cx[cx_index(g, s, k, j, f)];
     }
 }
 __device__ __forceinline__ void gather_y(const AdjArgs& a, int i, int w, double* Qb) {
@@ -337,8 +546,10 @@ __device__ __forceinline__ void gather_y(const AdjArgs& a, int i, int w, double*
     for (int s = 0; s < 4; ++s) {
         const int f = w + 2 - s;
         if (f < 0 || f > g.ny) continue;
+        const float* cf = reinterpret_cast<const float*>(a.Cy);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) Qb[k] += a.Cy[cy_index(g, s, k, f, i)];
+        for (int k = 0; k < NP; ++k)
+            Qb[k] += a.f32 ? (double)cf[cy_index(g, s, k, f, i)] : a.Cy[cy_index(g, s, k, f, i)];
     }
 }
 
@@ -469,18 +680,35 @@ extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Gr
 
 size_t adj_args_size() { return sizeof(AdjArgs); }
 
+// floats of the FP32 per-cell data of a grid (Pf, Vf, DX, DY, LX, LY)
+long long adj_f32_floats(const Grid2D& g) {
+    return 2LL * NP * g.fstride + (long long)NP * g.ny * (g.nx + 3) +
+           (long long)NP * (g.ny + 3) * g.nx + 4LL * g.ny * (g.nx + 2) + 4LL * (g.ny + 2) * g.nx;
+}
+
 // Host launcher of one stage reverse (declared in mxe_capi.cu).
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      bool f32, cudaStream_t st) {
+                      bool f32, float* f32buf, cudaStream_t st) {
     AdjArgs a;
     a.U = U; a.V = V; a.coef = coef; a.b1 = b1; a.b2 = b2; a.out = out;
+    a.f32 = f32 ? 1 : 0;
+    a.Pf = f32buf;
+    a.Vf = f32buf + (long long)NP * g.fstride;
+    a.DX = a.Vf + (long long)NP * g.fstride;
+    a.DY = a.DX + (long long)NP * g.ny * (g.nx + 3);
+    a.LX = a.DY + (long long)NP * (g.ny + 3) * g.nx;
+    a.LY = a.LX + 4LL * g.ny * (g.nx + 2);
     a.P = P; a.Cx = Cx; a.Cy = Cy; a.gbar = gbar; a.taubar = taubar;
     a.g = g; a.p = p;
     dim3 cg((g.nx + 127) / 128, g.ny);
     mxe_adj_prims<<<cg, 128, 0, st>>>(a);
     if (f32) {
+        const int npairs = (g.nx + 3) * g.ny + g.nx * (g.ny + 3);
+        mxe_adj_diffs<<<(npairs + 127) / 128, 128, 0, st>>>(a);
+        const int ncl = (g.nx + 2) * g.ny + g.nx * (g.ny + 2);
+        mxe_adj_limiters<<<(ncl + 127) / 128, 128, 0, st>>>(a);
         mxe_adj_faces_x_f32<<<dim3((g.nx + 1 + 63) / 64, g.ny), 128, 0, st>>>(a);
         mxe_adj_faces_y_f32<<<dim3((g.nx + 63) / 64, g.ny + 1), 128, 0, st>>>(a);
     } else {

@@ -184,10 +184,20 @@ __device__ __forceinline__ void lam_p_fwd(const DimlessP<T>& g, T sb, LamP<T>& L
     L.ssb = M<T>::sqrt_(sb);
     L.C = M<T>::sqrt_((T(3.0) - T(3.0) * sb) * L.Pkk);
     L.E = T(0.8) * L.C;
-    L.sR10 = M<T>::sqrt_(T(10.0) - T(16.0) * L.ssb + T(6.0) * sb);
+    // the forward's forms: printed in FP64; in FP32 the identical
+    // 2 (5 - 3r)(1 - r) and (sqrt B - E)^2, which cannot round below zero
+    if (sizeof(T) == 8)
+        L.sR10 = M<T>::sqrt_(T(10.0) - T(16.0) * L.ssb + T(6.0) * sb);
+    else
+        L.sR10 = M<T>::sqrt_(T(2.0) * (T(5.0) - T(3.0) * L.ssb) * (T(1.0) - L.ssb));
     const T B = T(5.0) - T(4.0) * L.ssb + L.sR10;
     L.sB = M<T>::sqrt_(B);
-    L.Y = B + L.E * L.E - T(2.0) * L.E * L.sB;
+    if (sizeof(T) == 8) {
+        L.Y = B + L.E * L.E - T(2.0) * L.E * L.sB;
+    } else {
+        const T dd = L.sB - L.E;
+        L.Y = dd * dd;
+    }
     L.poly = T(0.6) * L.Pkk * L.Pkk - T(0.38) * L.Pkk + T(0.35);
     const T al = L.qperp * L.poly;
     L.base = T(4.0) * sb * sb * L.Y + L.qperp * L.qperp / T(10.0);
@@ -848,25 +858,25 @@ struct PhiAdj {
     int ks;
 };
 
+// Shared limiter from the stencil differences dm = q0 - qm, dp = qp - q0.
 template <class T, int NF>
-__device__ __forceinline__ PhiAdj<T> phi_adj(const T* qm, const T* q0, const T* qp,
-                                          int lim) {
+__device__ __forceinline__ PhiAdj<T> phi_adj_d(const T* dm, const T* dp, int lim) {
     PhiAdj<T> r{T(1.0), T(0.0), T(0.0), -1};
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const T dm = q0[k] - qm[k], dp = qp[k] - q0[k];
-        const T pk = phi_field(dm, dp, lim);
+        const T pk = phi_field(dm[k], dp[k], lim);
         if (pk < r.phi) {
             r.phi = pk;
             r.ks = k;
-            if (mul_rn(dm, dp) > T(0.0)) {
+            if (mul_rn(dm[k], dp[k]) > T(0.0)) {
                 if (lim == 1) {
-                    const T s = dm * dm + dp * dp;
-                    r.ddm = T(2.0) * dp * (dp * dp - dm * dm) / (s * s);
-                    r.ddp = T(2.0) * dm * (dm * dm - dp * dp) / (s * s);
+                    const T s = dm[k] * dm[k] + dp[k] * dp[k];
+                    r.ddm = T(2.0) * dp[k] * (dp[k] * dp[k] - dm[k] * dm[k]) / (s * s);
+                    r.ddp = T(2.0) * dm[k] * (dm[k] * dm[k] - dp[k] * dp[k]) / (s * s);
                 } else {
-                    const T am = fabs(dm), ap = fabs(dp), s = am + ap;
-                    const T sm = dm > T(0.0) ? T(1.0) : -T(1.0), sp = dp > T(0.0) ? T(1.0) : -T(1.0);
+                    const T am = fabs(dm[k]), ap = fabs(dp[k]), s = am + ap;
+                    const T sm = dm[k] > T(0.0) ? T(1.0) : T(-1.0);
+                    const T sp = dp[k] > T(0.0) ? T(1.0) : T(-1.0);
                     if (am < ap) {
                         r.ddm = sm * T(2.0) * ap / (s * s);
                         r.ddp = -sp * T(2.0) * am / (s * s);
@@ -883,24 +893,32 @@ __device__ __forceinline__ PhiAdj<T> phi_adj(const T* qm, const T* q0, const T* 
     return r;
 }
 
-// Reverse of the MUSCL face value qf = q0 + hs (phi cen), cen = (qp - qm)/2
-// (computed as ((q0 - qm) + (qp - q0))/2), with phi = phi_{k*}(q0 - qm,
-// qp - q0): adjoint qfb -> contributions to the three stencil cells.  A
-// field that is flat across the stencil (both differences exactly zero)
-// has the zero slope, whose derivative is zero (the same choice as the
-// oracle's tangent): a perturbation of a flat stencil is limited, not
-// passed on with phi = 1.
 template <class T, int NF>
-__device__ __forceinline__ void muscl_bwd(const T* qm, const T* q0, const T* qp,
-                                          const PhiAdj<T>& ph, T hs, const T* qfb,
-                                          T* bm, T* b0, T* bp) {
+__device__ __forceinline__ PhiAdj<T> phi_adj(const T* qm, const T* q0, const T* qp, int lim) {
+    T dm[NF], dp[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dm[k] = q0[k] - qm[k];
+        dp[k] = qp[k] - q0[k];
+    }
+    return phi_adj_d<T, NF>(dm, dp, lim);
+}
+
+// Reverse of the MUSCL face value qf = q0 + hs (phi cen), cen = (dm + dp)/2,
+// phi = phi_{k*}(dm, dp), dm = q0 - qm, dp = qp - q0: adjoint qfb ->
+// contributions to the three stencil cells.  A field that is flat across the
+// stencil (both differences exactly zero) has the zero slope, whose
+// derivative is zero (the same choice as the oracle's tangent): a
+// perturbation of a flat stencil is limited, not passed on with phi = 1.
+template <class T, int NF>
+__device__ __forceinline__ void muscl_bwd_d(const T* dm, const T* dp, const PhiAdj<T>& ph, T hs,
+                                            const T* qfb, T* bm, T* b0, T* bp) {
     T phib = T(0.0);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const T dm = q0[k] - qm[k], dp = qp[k] - q0[k];
         b0[k] += qfb[k];
-        if (dm == T(0.0) && dp == T(0.0)) continue;
-        const T cen = T(0.5) * (dm + dp);
+        if (dm[k] == T(0.0) && dp[k] == T(0.0)) continue;
+        const T cen = T(0.5) * (dm[k] + dp[k]);
         const T cb = hs * ph.phi * qfb[k];
         bm[k] -= T(0.5) * cb;
         bp[k] += T(0.5) * cb;
@@ -916,6 +934,19 @@ __device__ __forceinline__ void muscl_bwd(const T* qm, const T* q0, const T* qp,
                 bp[k] += dpb;
             }
     }
+}
+
+template <class T, int NF>
+__device__ __forceinline__ void muscl_bwd(const T* qm, const T* q0, const T* qp,
+                                          const PhiAdj<T>& ph, T hs, const T* qfb, T* bm, T* b0,
+                                          T* bp) {
+    T dm[NF], dp[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dm[k] = q0[k] - qm[k];
+        dp[k] = qp[k] - q0[k];
+    }
+    muscl_bwd_d<T, NF>(dm, dp, ph, hs, qfb, bm, b0, bp);
 }
 
 }  // namespace adj

@@ -47,7 +47,8 @@ const void* tubes_mixed_kernel(bool planar, int nt);
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      bool f32, cudaStream_t st);
+                      bool f32, float* f32buf, cudaStream_t st);
+long long adj_f32_floats(const Grid2D& g);
 extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g,
                                         int to_pitched);
 size_t tubes_mixed_smem(bool planar, int nt);
@@ -111,6 +112,7 @@ struct mxe_ctx {
     double* adjB = nullptr;
     double* adjG = nullptr;           // [4][GHOST_SLOTS][14] imposed-state adjoint, then tau_ref's
     bool adj_f32 = false;             // face-state reverse in FP32 (MXE_MIXED adjoint)
+    float* adjF = nullptr;            // FP32 per-cell data of that reverse
     // state
     double* U = nullptr;
     double* Us = nullptr;
@@ -423,6 +425,7 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->adjA);
     cudaFree(c->adjB);
     cudaFree(c->adjG);
+    cudaFree(c->adjF);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -676,8 +679,9 @@ static mxe_status periodic_ok(mxe_ctx* c) {
 // One step of a 2D grid.  ustar (FP64 RK2 only, optional): where stage 1
 // writes U* (default: the context's stage buffer).
 static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
-                                 double* ustar = nullptr) {
+                                 double* ustar = nullptr, bool skip_rate = false) {
     Stage2DArgs a{};
+    a.skip_rate = skip_rate && !c->mixed;
     a.dt_hist = c->dth;
     a.dt_hist_cap = c->dth_cap;
     a.g = c->g;
@@ -1228,6 +1232,7 @@ static mxe_status adjoint_ready(mxe_ctx* c) {
         CK(cudaMalloc(&c->adjB, sizeof(double) * c->nelem));
         CK(cudaMalloc(&c->adjG, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1)));
     }
+    if (c->adj_f32 && !c->adjF) CK(cudaMalloc(&c->adjF, sizeof(float) * adj_f32_floats(c->g)));
     return MXE_OK;
 }
 
@@ -1258,8 +1263,16 @@ extern "C" mxe_status mxe_adjoint_record(mxe_ctx* c, int n, const double* dts) {
         double* un = c->tape + c->nelem * (long long)(rk2 ? 2 * i : i);
         CK(cudaMemcpyAsync(un, c->U, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
                            c->stream));
-        s = launch_2d_step(c, INFINITY, dts[i], rk2 ? un + c->nelem : nullptr);
+        s = launch_2d_step(c, INFINITY, dts[i], rk2 ? un + c->nelem : nullptr, true);
         if (s != MXE_OK) return s;
+    }
+    // the replay skipped the CFL rate: form it once for the final state
+    {
+        DevClock* ck = c->clk;
+        CK(cudaMemsetAsync(&ck->rate[c->slot], 0, sizeof(unsigned long long), c->stream));
+        dim3 grid((c->g.nx + 255) / 256, c->g.ny);
+        mxe_rate14_2d_planar<<<grid, 256, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, c->slot);
+        CK(cudaGetLastError());
     }
     c->tape_n = n;
     c->tape_dt.assign(dts, dts + n);
@@ -1295,14 +1308,14 @@ extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, d
         if (rk2) {
             // U^{n+1} = U^n + dt L(U*): B = dt L'(U*)^T A
             e = adj_stage(un + c->nelem, c->adjA, dt, nullptr, nullptr, c->adjB, c->adjP,
-                          c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
+                          c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
             // U* = U^n + dt/2 L(U^n): A = A + B + dt/2 L'(U^n)^T B
             if (e == cudaSuccess)
                 e = adj_stage(un, c->adjB, 0.5 * dt, c->adjA, c->adjB, c->adjA, c->adjP,
-                              c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
+                              c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
         } else {
             e = adj_stage(un, c->adjA, dt, c->adjA, nullptr, c->adjA, c->adjP, c->adjCx,
-                          c->adjCy, gb, tb, g, p, c->adj_f32, c->stream);
+                          c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
         }
         if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint stage: %s", cudaGetErrorString(e));
     }
@@ -1353,7 +1366,7 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
     CK(cudaMalloc(&Op, sizeof(double) * c->nelem));
     cudaError_t e = adj_stage(Up, Vp, 1.0, nullptr, nullptr, Op, c->adjP, c->adjCx, c->adjCy,
                               c->adjG, c->adjG + 4 * GHOST_SLOTS * 14, g, p, c->adj_f32,
-                              c->stream);
+                              c->adjF, c->stream);
     if (e == cudaSuccess) {
         double* dst = on_device ? out : tmpU;
         mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0);

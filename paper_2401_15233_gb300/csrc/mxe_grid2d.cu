@@ -293,11 +293,13 @@ __device__ __forceinline__ void stage_f64(const Stage2DArgs& a) {
                 PH::cons2prim_rn(Un, Qn);
                 if (PH::nonpositive(Qn)) atomicOr(&a.clk->status, ST_NONPOSITIVE);
                 if (bad) atomicOr(&a.clk->status, ST_NONFINITE);
-                double ax, ay;
-                PH::rates(Qn, p.sigma_lim, p.k_ws, ax, ay);
-                r = ax * g.idx;
-                r = r + ay * g.idy;
-                if (!(r >= 0.0)) r = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> inf
+                if (!a.skip_rate) {
+                    double ax, ay;
+                    PH::rates(Qn, p.sigma_lim, p.k_ws, ax, ay);
+                    r = ax * g.idx;
+                    r = r + ay * g.idy;
+                    if (!(r >= 0.0)) r = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> inf
+                }
             }
         }
     }

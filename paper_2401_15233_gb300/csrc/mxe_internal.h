@@ -59,6 +59,7 @@ struct Stage2DArgs {
     DevClock* clk;
     double* dt_hist;                // optional: dt of step s at dt_hist[s] (s < dt_hist_cap)
     long long dt_hist_cap;
+    int skip_rate;                  // FP64 final stage: no CFL rate (prescribed dt follows)
 };
 
 // ---- 1D tubes ----
