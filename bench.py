@@ -61,6 +61,8 @@ def parse():
                    help="skip the batched-tube leg (256 Sod tubes, one graph launch)")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint leg (512^2 crossed jets, 500 steps, checkpoints every 50)")
+    p.add_argument("--no-jet", action="store_true",
+                   help="skip the single collisionless jet leg (1200^2, forward Euler)")
     p.add_argument("--only", default=None, choices=["batch", "adjoint"],
                    help="run one secondary leg alone (profiling runs)")
     p.add_argument("--batch-t-end", type=float, default=0.2)
@@ -152,15 +154,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU (torchrun env).  Replicas: the only collective is
+    the max over ranks of the timed region."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend or "nccl")
     return world, rank, local, dist
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """max of a per-rank float over all ranks (identity without a group)"""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, total_ms):
+    """throughput of all ranks' units over the slowest rank's time (weak scaling)"""
+    return world * units_per_rank / (total_ms * 1e-3)
 
 
 def make_solver(mx, wl, n, precision, setup):
@@ -263,6 +282,42 @@ def bench_batch(mx, wl, stream, world, t_end=0.2):
                            "fp64": world * cu_f / (ms_f * 1e-3),
                            "speedup": (cu_w / ms_w) / (cu_f / ms_f), "unit": UNIT},
     }
+
+
+def bench_single_jet(mx, wl, stream, world, n=1200):
+    """Sec. 6 single collisionless jet (Mach 5, width L/7, background 1e-5,
+    no collision source), 1200^2, MUSCL + forward Euler, CFL 0.5, from the
+    background: cell-updates/s of the mixed and the FP64 paths (steps 5..25
+    and 5..15), and the step sizes seen."""
+    import numpy as np
+    import torch
+    setup = wl.collisionless_jets_setup(1)
+    lo, hi = setup["slot"]
+    prim = np.ascontiguousarray(np.moveaxis(wl.jets_initial(n, n, setup), -1, 0))
+    out = {"workload": f"single collisionless jet {n}x{n}, Mach 5, FE MUSCL HLL minmod, CFL 0.5"}
+    for prec, steps in (("mixed", 20), ("fp64", 10)):
+        s = mx.Solver(system=14, nx=n, ny=n, precision=prec, order=2, integrator="fe",
+                      flux="hll", limiter="minmod", cfl=0.5, sigma_lim=1e-4)
+        s.set_stream(stream.cuda_stream)
+        for side in (mx.XLO, mx.XHI, mx.YLO, mx.YHI):
+            s.set_bc(side, mx.BC_DIRICHLET, 0.0, 0.0, setup["background"])
+        s.set_bc(mx.XLO, mx.BC_DIRICHLET, lo, hi, setup["left"])
+        s.set_state(prim)
+        s.set_dt_history(5 + steps)
+        s.step(5, float("inf"), sync=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps, float("inf"), sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        dts = s.dt_history(5 + steps)
+        out[prec] = {"value": whole_job_value(n * n * steps, world, ms), "unit": UNIT,
+                     "ms_per_step": ms / steps, "dt_first": float(dts[0]), "dt_last": float(dts[-1])}
+        del s
+    out["speedup"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
@@ -409,20 +464,17 @@ def main():
             sampler.__exit__()
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist)
         return s, per, total_ms, sampler
 
     s, per, total_ms, clk = timed(args.precision, args.steps, True)
     d = s.diagnostics()
     planar = bool(d["planar"])
-    value = world * ncell * args.steps / (total_ms * 1e-3)
+    value = whole_job_value(ncell * args.steps, world, total_ms)
     other = "fp64" if args.precision == "mixed" else "mixed"
     csteps = args.compare_steps or args.steps
     s2, per2, total2, _ = timed(other, csteps, False)
-    other_value = world * ncell * csteps / (total2 * 1e-3)
+    other_value = whole_job_value(ncell * csteps, world, total2)
     planar2 = bool(s2.diagnostics()["planar"])
     del s2
 
@@ -484,6 +536,8 @@ def main():
         out["batch"] = bench_batch(mx, wl, stream, world, args.batch_t_end)
     if not args.no_adjoint:
         out["adjoint"] = bench_adjoint(world)
+    if not args.no_jet:
+        out["single_jet"] = bench_single_jet(mx, wl, stream, world)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(finite_json(out)), flush=True)

@@ -89,6 +89,24 @@ def jets_setup(mach=(3.0, 3.0), rho_bg=1e-3, T_bg=1.0, rho_jet=1.0, T_jet=1.0,
                 rho_ref=rho_jet, T_ref=T_jet, Kn=Kn)
 
 
+def collisionless_jets_setup(n_jets=1, mach=5.0, rho_jet=1.0, T_jet=1.0, bg_ratio=1e-5,
+                            jet_width=1.0 / 7.0):
+    """Collisionless jets into a near vacuum (Sec. 6): jets of width L/7
+    centred on the left wall (and, for two jets, the bottom wall), Mach 5,
+    Maxwellian at (rho_jet, T_jet); every other boundary cell holds the
+    background, rho_0 = 1e-5 rho_jet at T_jet and rest; no collision source.
+    The solution of the homogeneous system is self-similar in the density,
+    so rho_jet = 1.  Returns the background and jet primitives and the span."""
+    a = math.sqrt(GAMMA_3D * T_jet)
+    lo, hi = 0.5 - 0.5 * jet_width, 0.5 + 0.5 * jet_width
+    out = dict(background=maxwellian14(bg_ratio * rho_jet, 0.0, 0.0, T_jet),
+               left=maxwellian14(rho_jet, mach * a, 0.0, T_jet), slot=(lo, hi),
+               n_jets=n_jets)
+    if n_jets == 2:
+        out["bottom"] = maxwellian14(rho_jet, 0.0, mach * a, T_jet)
+    return out
+
+
 def jets_initial(nx: int, ny: int, setup: dict):
     """Uniform background (ny, nx, 14)."""
     return np.broadcast_to(setup["background"], (ny, nx, 14)).copy()
