@@ -35,6 +35,9 @@ extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const Param
 extern "C" __global__ void mxe_stage14_2d_mixed_planar(const Stage2DArgs a,
                                                        const ParamsT<float> p,
                                                        const MixedPolicy mp);
+extern "C" __global__ void mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a,
+                                                          const ParamsT<float> p,
+                                                          const MixedPolicy mp);
 extern "C" __global__ void mxe_resync14_2d(const double* U, float* W, Grid2D g);
 extern "C" __global__ void mxe_resync14_2d_planar(const double* U, float* W, Grid2D g);
 extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, ParamsT<float> p,
@@ -42,7 +45,7 @@ extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, ParamsT
 extern "C" __global__ void mxe_rate14_2d_mixed_planar(const float* W, Grid2D g,
                                                       ParamsT<float> p, float idxf, float idyf,
                                                       DevClock* clk, int slot);
-size_t stage14_2d_mixed_smem(bool planar);
+size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm);
 const void* tubes_mixed_kernel(bool planar, int nt);
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
@@ -64,7 +67,10 @@ extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const dou
                                           double* dst);
 extern "C" __global__ void mxe_k_ghost(int nf, int n, const double* in, double* out);
 extern "C" __global__ void mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim,
-                                      double* acc, unsigned long long* cnt);
+                                      double* part);
+extern "C" __global__ void mxe_k_diag_reduce(const double* part, long long nblocks,
+                                             double* acc);
+constexpr int DIAG_W = 24;
 }  // namespace mxe
 
 using namespace mxe;
@@ -118,9 +124,12 @@ struct mxe_ctx {
     double* Us = nullptr;
     float* W = nullptr;               // mixed: FP32 primitives of U
     float* Ws = nullptr;              // mixed: FP32 primitives of the stage state
+    double* diag_part = nullptr;      // diagnostics: per-block partials
+    long long diag_part_n = 0;
     bool mixed = false;
     MixedPolicy mp{0.0f, 0.999f, 1e-3f};
     int resync_every = 16;
+    int stage_occ = 3;                // planar mixed stage kernel: blocks per SM (2 or 3)
     long long launched = 0;           // steps launched since set_state
     bool state_planar = false;        // z-odd moments exactly zero (and kept so)
     bool w_planar = false;            // layout of W (mixed): compact planar fields
@@ -333,16 +342,20 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
     if (!c->tubes) {
         cudaError_t e = c->mixed
             ? cudaFuncSetAttribute(mxe_stage14_2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)stage14_2d_mixed_smem(false))
+                                   (int)stage14_2d_mixed_smem(false, 2))
             : cudaFuncSetAttribute(mxe_stage14_2d_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)stage14_2d_f64_smem(false));
         if (e == cudaSuccess)
             e = c->mixed ? cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)stage14_2d_mixed_smem(true))
+                                                (int)stage14_2d_mixed_smem(true, 2))
                          : cudaFuncSetAttribute(mxe_stage14_2d_f64_planar,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)stage14_2d_f64_smem(true));
+        if (e == cudaSuccess && c->mixed)
+            e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar_b3,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)stage14_2d_mixed_smem(true, 3));
         if (e != cudaSuccess) {
             fail(c, MXE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
             mxe_destroy(c);
@@ -406,6 +419,7 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->Us);
     cudaFree(c->W);
     cudaFree(c->Ws);
+    cudaFree(c->diag_part);
     cudaFree(c->stage);
     cudaFree(c->scratch);
     cudaFree(c->accd);
@@ -699,19 +713,28 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
     const bool pl = use_planar(c);
     if (c->mixed) {
         if (c->w_planar != pl) launch_resync(c, pl);       // W layout follows the kernel
-        auto kern = pl ? mxe_stage14_2d_mixed_planar : mxe_stage14_2d_mixed;
-        size_t sm = stage14_2d_mixed_smem(pl);
+        // planar state: three blocks per SM (no prefetch) or two (with the
+        // final-stage prefetch)
+        auto kern_of = [&](bool) {
+            if (!pl) return std::make_pair(mxe_stage14_2d_mixed, stage14_2d_mixed_smem(false, 2));
+            return c->stage_occ == 3 ? std::make_pair(mxe_stage14_2d_mixed_planar_b3,
+                                                      stage14_2d_mixed_smem(true, 3))
+                                     : std::make_pair(mxe_stage14_2d_mixed_planar,
+                                                      stage14_2d_mixed_smem(true, 2));
+        };
         ParamsT<float> fp = fparams(c);
         a.Ubase = c->U;
         a.Uout = c->U;
         if (c->cfg.integrator == MXE_RK2) {
+            auto k1 = kern_of(false), k2 = kern_of(true);
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
-            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
+            k1.first<<<grid, 256, k1.second, c->stream>>>(a, fp, c->mp);
             a.Win = c->Ws; a.Wout = c->W; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
+            k2.first<<<grid, 256, k2.second, c->stream>>>(a, fp, c->mp);
         } else {
+            auto k2 = kern_of(true);
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            kern<<<grid, 256, sm, c->stream>>>(a, fp, c->mp);
+            k2.first<<<grid, 256, k2.second, c->stream>>>(a, fp, c->mp);
             std::swap(c->W, c->Ws);
         }
         CK(cudaGetLastError());
@@ -1033,6 +1056,15 @@ extern "C" mxe_status mxe_set_mixed_policy(mxe_ctx* c, double sigma_lo, double s
     return MXE_OK;
 }
 
+extern "C" mxe_status mxe_set_stage_occupancy(mxe_ctx* c, int blocks_per_sm) {
+    if (!c) return MXE_EINVAL;
+    if (!c->mixed || c->tubes) return fail(c, MXE_ESTATE, "not a 2D MXE_MIXED context");
+    if (blocks_per_sm != 2 && blocks_per_sm != 3)
+        return fail(c, MXE_EINVAL, "blocks_per_sm must be 2 or 3");
+    c->stage_occ = blocks_per_sm;
+    return MXE_OK;
+}
+
 extern "C" mxe_status mxe_batch_run(mxe_ctx* c, int max_steps, double t_end) {
     if (!c) return MXE_EINVAL;
     if (!c->tubes) return fail(c, MXE_ESTATE, "not a batch context");
@@ -1144,23 +1176,27 @@ extern "C" mxe_status mxe_get_diagnostics(mxe_ctx* c, mxe_diag* out) {
     if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
     memset(out, 0, sizeof *out);
     double acc[32];
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-    acc[16] = INFINITY;
-    unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    CK(cudaMemcpyAsync(c->accd, acc, sizeof acc, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->scratch, cnt, sizeof cnt, cudaMemcpyHostToDevice, c->stream));
-    mxe_k_diag<<<cellgrid(c, 128), 128, 0, c->stream>>>(cellmap(c), c->nf, c->U,
-                                                        c->cfg.sigma_lim, c->accd, c->scratch);
+    dim3 dg = cellgrid(c, 128);
+    long long nb = (long long)dg.x * dg.y;
+    if (c->diag_part_n < nb) {
+        cudaFree(c->diag_part);
+        c->diag_part = nullptr;
+        c->diag_part_n = 0;
+        CK(cudaMalloc(&c->diag_part, sizeof(double) * DIAG_W * nb));
+        c->diag_part_n = nb;
+    }
+    mxe_k_diag<<<dg, 128, 0, c->stream>>>(cellmap(c), c->nf, c->U, c->cfg.sigma_lim,
+                                          c->diag_part);
+    mxe_k_diag_reduce<<<1, 256, 0, c->stream>>>(c->diag_part, nb, c->accd);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(acc, c->accd, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(cnt, c->scratch, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(acc, c->accd, sizeof(double) * 21, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < c->nf; ++k) out->sums[k] = acc[k];
     out->min_sigma = acc[16];
-    out->n_sigma_below_lim = (long long)cnt[0];
-    out->n_sigma_above_one = (long long)cnt[1];
-    out->n_nonpositive = (long long)cnt[2];
-    out->n_nonfinite = (long long)cnt[3];
+    out->n_sigma_below_lim = (long long)acc[17];
+    out->n_sigma_above_one = (long long)acc[18];
+    out->n_nonpositive = (long long)acc[19];
+    out->n_nonfinite = (long long)acc[20];
     if (c->tubes) {
         std::vector<TubeClock> h(c->ntubes);
         CK(cudaMemcpy(h.data(), c->tclk, sizeof(TubeClock) * c->ntubes, cudaMemcpyDeviceToHost));

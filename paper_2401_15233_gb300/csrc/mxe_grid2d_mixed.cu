@@ -180,17 +180,18 @@ __device__ __forceinline__ double step_dt_m(const DevClock* clk, int slot, doubl
 }
 
 // Own-cell prefetch of the final stage (U^n FP64 and W^n FP32 into shared
-// memory at kernel start): on for the ten-field planar state, where it
-// still fits two blocks per SM.
-template <int NF>
-constexpr int prefetch_cells() { return NF == NP ? TXm * TYm : 0; }
+// memory at kernel start): an option of the ten-field planar state at two
+// blocks per SM (at three blocks per SM its shared memory does not fit, and
+// the same cells are prefetched into L2 instead).
+template <int NF, bool PFON>
+constexpr int prefetch_cells() { return (PFON && NF == NP) ? TXm * TYm : 0; }
 
 // shared memory: own-cell prefetch, stencil box, x and y face fluxes,
 // staged left face states, limiters, reduction scratch
-template <int NF>
+template <int NF, bool PFON>
 constexpr size_t smem_mixed() {
-    return sizeof(double) * (NF * prefetch_cells<NF>()) +
-           sizeof(float) * (NF * prefetch_cells<NF>() + NF * NBOXm + 2 * NF * NTm +
+    return sizeof(double) * (NF * prefetch_cells<NF, PFON>()) +
+           sizeof(float) * (NF * prefetch_cells<NF, PFON>() + NF * NBOXm + 2 * NF * NTm +
                             (2 * NF + 2) * NTm + NPHXm + NPHYm + 8);
 }
 
@@ -204,12 +205,12 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 }
 
 
-template <class PH>
+template <class PH, bool PFON>
 __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<float>& p,
                                             const MixedPolicy& mp) {
     constexpr int NF = PH::NF;
     constexpr int NC = TXm * TYm;
-    constexpr int PF = prefetch_cells<NF>();
+    constexpr int PF = prefetch_cells<NF, PFON>();
     extern __shared__ __align__(16) double smd[];
     double* Upf = smd;                               // [NF][PF] own-cell U^n (final stage)
     float* Wpf = (float*)(Upf + NF * PF);            // [NF][PF] own-cell W^n (final stage)
@@ -255,12 +256,19 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
     const bool inside = owner && gi < g.nx && gj < g.ny;
     const long long o = (long long)gj * g.pitch + gi;
     // final stage: start fetching this cell's U^n and W^n now; they are
-    // needed only after all face fluxes are done
+    // needed only after all face fluxes are done (into shared memory, or
+    // into L2 where there is no room)
     if (PF && a.final_stage && inside) {
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             cp_async8(Upf + k * PF + tid, a.Ubase + o + PH::ufield(k) * g.fstride);
             cp_async4(Wpf + k * PF + tid, a.Wbase + o + k * g.fstride);
+        }
+    } else if (a.final_stage && inside) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Ubase + o + PH::ufield(k) * g.fstride));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Wbase + o + k * g.fstride));
         }
     }
     asm volatile("cp.async.commit_group;\n" ::);
@@ -371,15 +379,22 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
 
 extern "C" __global__ void __launch_bounds__(NTm, 2)
 mxe_stage14_2d_mixed(const Stage2DArgs a, const ParamsT<float> p, const MixedPolicy mp) {
-    stage_mixed<PhysGeneral>(a, p, mp);
+    stage_mixed<PhysGeneral, false>(a, p, mp);
 }
 extern "C" __global__ void __launch_bounds__(NTm, 2)
 mxe_stage14_2d_mixed_planar(const Stage2DArgs a, const ParamsT<float> p, const MixedPolicy mp) {
-    stage_mixed<PhysPlanar>(a, p, mp);
+    stage_mixed<PhysPlanar, true>(a, p, mp);
+}
+// planar state at three blocks per SM (at most 80 registers, L2 prefetch)
+extern "C" __global__ void __launch_bounds__(NTm, 3)
+mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a, const ParamsT<float> p,
+                               const MixedPolicy mp) {
+    stage_mixed<PhysPlanar, false>(a, p, mp);
 }
 
-size_t stage14_2d_mixed_smem(bool planar) {
-    return planar ? smem_mixed<NP>() : smem_mixed<14>();
+size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm) {
+    if (!planar) return smem_mixed<14, false>();
+    return blocks_per_sm >= 3 ? smem_mixed<NP, false>() : smem_mixed<NP, true>();
 }
 
 // W = FP32 primitives of U, converted in FP64 (set-up and periodic re-sync).

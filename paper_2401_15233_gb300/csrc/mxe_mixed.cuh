@@ -39,18 +39,22 @@ __device__ __forceinline__ bool face_state_m(const float* Qf, const ParamsT<floa
                                              float* out) {
     constexpr int NF = PH::NF;
     float lo, hi;
-    PH::template face<float, K>(Qf, p.sigma_lim, p.k_ws, out, out + NF, lo, hi);
-    out[2 * NF] = lo;
-    out[2 * NF + 1] = hi;
     bool flag = false;
     if (mp.sig_lo > 0.0f || mp.sig_hi < 1.0f || mp.det_min > 0.0f) {
+        // the conditioning comes out of the same evaluation
         float sig, det;
-        PH::conditioning(Qf, sig, det);
+        PH::template face_c<float, K>(Qf, p.sigma_lim, p.k_ws, out, out + NF, lo, hi, sig, det);
+        out[2 * NF] = lo;
+        out[2 * NF + 1] = hi;
         flag = (sig >= p.sigma_lim && sig < mp.sig_lo) || sig > mp.sig_hi || det < mp.det_min ||
                !(sig == sig);
         if (__any_sync(__activemask(), flag)) {
             if (flag) face_fp64<PH, K>(Qf, sl64, kw64, out);
         }
+    } else {
+        PH::template face<float, K>(Qf, p.sigma_lim, p.k_ws, out, out + NF, lo, hi);
+        out[2 * NF] = lo;
+        out[2 * NF + 1] = hi;
     }
     return flag;
 }

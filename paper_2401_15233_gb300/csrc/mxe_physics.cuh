@@ -570,6 +570,26 @@ __device__ __forceinline__ void face_eval14(const T* Q, T sigma_lim, T k_ws, T* 
     lmin = Q[1 + K] + k_ws * lm * d.sq;
 }
 
+// The same, also returning the raw sigma and det P* of the state (the
+// conditioning of its closure).
+template <class T, int K>
+__device__ __forceinline__ void face_eval14(const T* Q, T sigma_lim, T k_ws, T* U, T* F,
+                                            T& lmin, T& lmax, T& sig, T& det) {
+    Dimless14<T> d;
+    dimless14(Q, d);
+    T sb = clamp_sigma(d.sig, sigma_lim);
+    T Qk[6], Rk[3], Sk;
+    closure14_slice<T, K>(Q, d, sb, Qk, Rk, Sk);
+    prim2cons14(Q, U);
+    flux14<T, K>(Q, U, Qk, Rk, Sk, F);
+    T lp, lm;
+    lam14_star<T, K>(d, sb, lp, lm);
+    lmax = Q[1 + K] + k_ws * lp * d.sq;
+    lmin = Q[1 + K] + k_ws * lm * d.sq;
+    sig = d.sig;
+    det = d.det;
+}
+
 template <class T, int K>
 __device__ __forceinline__ void face_eval14(const T* Q, const SchemeParams& sp, T* U, T* F,
                                             T& lmin, T& lmax) {

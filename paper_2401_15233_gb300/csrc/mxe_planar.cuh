@@ -239,6 +239,25 @@ __device__ __forceinline__ void face_eval_p(const T* Q, T sigma_lim, T k_ws, T* 
     lmin = Q[1 + K] + k_ws * lm * g.sq;
 }
 
+// The same, also returning the raw sigma and det P* of the state.
+template <class T, int K>
+__device__ __forceinline__ void face_eval_p(const T* Q, T sigma_lim, T k_ws, T* U, T* F, T& lmin,
+                                            T& lmax, T& sig, T& det) {
+    DimlessP<T> g;
+    dimless_p(Q, g);
+    T sb = clamp_sigma(g.sig, sigma_lim);
+    T QK[4], RK[2], SK;
+    closure_p<T, K>(Q, g, sb, QK, RK, SK);
+    prim2cons_p(Q, U);
+    flux_p<T, K>(Q, U, QK, RK, SK, F);
+    T lp, lm;
+    lam_p<T, K>(g, sb, lp, lm);
+    lmax = Q[1 + K] + k_ws * lp * g.sq;
+    lmin = Q[1 + K] + k_ws * lm * g.sq;
+    sig = g.sig;
+    det = g.det;
+}
+
 template <class T, int K>
 __device__ __forceinline__ T amax_p(const T* Q, const DimlessP<T>& g, T sigma_lim, T k_ws) {
     T sb = clamp_sigma(g.sig, sigma_lim);

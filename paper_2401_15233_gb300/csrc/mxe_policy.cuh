@@ -40,6 +40,12 @@ struct PhysGeneral {
     static __device__ __forceinline__ void face(const T* Q, T sl, T kw, T* U, T* F, T& lo, T& hi) {
         face_eval14<T, K>(Q, sl, kw, U, F, lo, hi);
     }
+    // with the conditioning of the closure (raw sigma, det P*)
+    template <class T, int K>
+    static __device__ __forceinline__ void face_c(const T* Q, T sl, T kw, T* U, T* F, T& lo,
+                                                  T& hi, T& sig, T& det) {
+        face_eval14<T, K>(Q, sl, kw, U, F, lo, hi, sig, det);
+    }
     // conditioning of the closure at a face state: raw sigma and det P*
     template <class T>
     static __device__ __forceinline__ void conditioning(const T* Q, T& sig, T& det) {
@@ -88,6 +94,11 @@ struct PhysPlanar {
     template <class T, int K>
     static __device__ __forceinline__ void face(const T* Q, T sl, T kw, T* U, T* F, T& lo, T& hi) {
         face_eval_p<T, K>(Q, sl, kw, U, F, lo, hi);
+    }
+    template <class T, int K>
+    static __device__ __forceinline__ void face_c(const T* Q, T sl, T kw, T* U, T* F, T& lo,
+                                                  T& hi, T& sig, T& det) {
+        face_eval_p<T, K>(Q, sl, kw, U, F, lo, hi, sig, det);
     }
     template <class T>
     static __device__ __forceinline__ void conditioning(const T* Q, T& sig, T& det) {

@@ -124,37 +124,93 @@ extern "C" __global__ void mxe_k_ghost(int nf, int n, const double* in, double* 
     for (int k = 0; k < 14; ++k) out[s * 14 + k] = k < nf ? Q[k] : 0.0;
 }
 
-// Diagnostics: acc[0..nf) field sums, acc[16] min sigma;
-// cnt[0] sigma<lim, cnt[1] sigma>1, cnt[2] non-positive, cnt[3] non-finite.
-__device__ __forceinline__ void atomic_min_double(double* a, double v) {
-    unsigned long long* p = (unsigned long long*)a;
-    unsigned long long old = *p, assumed;
-    do {
-        assumed = old;
-        if (__longlong_as_double((long long)assumed) <= v) return;
-        old = atomicCAS(p, assumed, (unsigned long long)__double_as_longlong(v));
-    } while (old != assumed);
+// Diagnostics in two passes with a fixed summation order (the result does
+// not depend on the scheduling of blocks).  Pass 1: each block writes
+// DIAG_W partials: [0, nf) field sums over its cells, [16] min raw sigma,
+// [17] sigma < sigma_lim, [18] sigma > 1, [19] non-positive, [20]
+// non-finite cell counts (counts held exactly as doubles).
+constexpr int DIAG_W = 24;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-extern "C" __global__ void mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim,
-                                      double* acc, unsigned long long* cnt) {
+extern "C" __global__ void __launch_bounds__(128)
+mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim, double* part) {
+    __shared__ double sh[4][DIAG_W];
+    double v[DIAG_W];
+#pragma unroll
+    for (int k = 0; k < DIAG_W; ++k) v[k] = 0.0;
+    v[16] = INFINITY;
     long long dense, dfs, dev, fs, idx;
-    if (!cell_of(m, dense, dfs, dev, fs, idx)) return;
-    double V[14], Q[14];
-    bool fin = true;
-    for (int k = 0; k < nf; ++k) {
-        V[k] = U[dev + k * fs];
-        fin &= isfinite(V[k]);
-        atomicAdd(acc + k, V[k]);
+    if (cell_of(m, dense, dfs, dev, fs, idx)) {
+        double V[14], Q[14];
+        for (int k = 0; k < nf; ++k) V[k] = U[dev + k * fs];
+        bool fin = true;
+        for (int k = 0; k < nf; ++k) {
+            fin &= isfinite(V[k]);
+            v[k] = V[k];
+        }
+        if (!fin) {
+            v[20] = 1.0;
+        } else {
+            to_prim(V, Q, nf);
+            bool pos = Q[0] > 0.0 &&
+                       (nf == 5 ? Q[2] > 0.0 : (Q[4] > 0.0 && Q[7] > 0.0 && Q[9] > 0.0));
+            if (!pos) {
+                v[19] = 1.0;
+            } else {
+                double sg = raw_sigma(Q, nf);
+                v[17] = sg < sigma_lim ? 1.0 : 0.0;
+                v[18] = sg > 1.0 ? 1.0 : 0.0;
+                v[16] = sg;
+            }
+        }
     }
-    if (!fin) { atomicAdd(cnt + 3, 1ull); return; }
-    to_prim(V, Q, nf);
-    bool pos = Q[0] > 0.0 && (nf == 5 ? Q[2] > 0.0 : (Q[4] > 0.0 && Q[7] > 0.0 && Q[9] > 0.0));
-    if (!pos) { atomicAdd(cnt + 2, 1ull); return; }
-    double s = raw_sigma(Q, nf);
-    if (s < sigma_lim) atomicAdd(cnt + 0, 1ull);
-    if (s > 1.0) atomicAdd(cnt + 1, 1ull);
-    atomic_min_double(acc + 16, s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < DIAG_W; ++k) {
+        double r = k == 16 ? warp_min_d(v[k]) : warp_sum_d(v[k]);
+        if (lane == 0) sh[w][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < DIAG_W) {
+        int k = threadIdx.x;
+        double r = sh[0][k];
+        for (int q = 1; q < 4; ++q) r = k == 16 ? fmin(r, sh[q][k]) : r + sh[q][k];
+        part[((long long)blockIdx.y * gridDim.x + blockIdx.x) * DIAG_W + k] = r;
+    }
+}
+
+// Pass 2 (one block of 256 threads): acc[k] = the partials combined, each
+// thread over a fixed stride of blocks, then a fixed tree.
+extern "C" __global__ void __launch_bounds__(256)
+mxe_k_diag_reduce(const double* part, long long nblocks, double* acc) {
+    __shared__ double sh[256];
+    for (int k = 0; k < 21; ++k) {
+        double r = k == 16 ? INFINITY : 0.0;
+        for (long long b = threadIdx.x; b < nblocks; b += 256) {
+            double x = part[b * DIAG_W + k];
+            r = k == 16 ? fmin(r, x) : r + x;
+        }
+        sh[threadIdx.x] = r;
+        __syncthreads();
+        for (int h = 128; h > 0; h >>= 1) {
+            if (threadIdx.x < h)
+                sh[threadIdx.x] = k == 16 ? fmin(sh[threadIdx.x], sh[threadIdx.x + h])
+                                          : sh[threadIdx.x] + sh[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) acc[k] = sh[0];
+        __syncthreads();
+    }
 }
 
 }  // namespace mxe

@@ -182,3 +182,27 @@ def test_mixed_sampled_4096_bench_config(mx, orc):
         print(f"window {(i0, j0)}: mixed {e.max():.2e}, sensitivity {sens.max():.2e}")
         assert np.all(e <= 10 * np.maximum(sens, 1e-12)), ((i0, j0), e, sens)
         assert np.all(np.linalg.norm(got, axis=0)[~ok] == 0)
+
+
+def test_stage_occupancy_same_result(mx):
+    """The planar stage kernel at two blocks per SM (shared-memory prefetch)
+    and at three (80 registers, L2 prefetch) computes the same arithmetic:
+    bitwise equal states and step sizes after 20 steps with a re-sync; the
+    setter rejects other shapes and other contexts."""
+    n = 200
+    setup = wl.jets_setup(Kn=0.1)
+    prim = aos_to_soa(wl.jets_like_field(n, n, setup))
+    out = {}
+    for occ in (2, 3):
+        s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+        s.set_stage_occupancy(occ)
+        s.set_state(prim)
+        s.step(20, float("inf"))
+        out[occ] = (s.get_moments("conserved"), s.diagnostics()["t"])
+        assert s.diagnostics()["planar"] == 1
+    assert np.array_equal(out[2][0], out[3][0]) and out[2][1] == out[3][1]
+    with pytest.raises(mx.MaxentError):
+        s.set_stage_occupancy(4)
+    f = jets_gpu_solver(mx, 16, 16, setup, precision="fp64")
+    with pytest.raises(mx.MaxentError):
+        f.set_stage_occupancy(3)

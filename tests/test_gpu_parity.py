@@ -465,3 +465,29 @@ def test_crossing_collisionless_jets_dt_history(mx, orc):
         print(f"  step {k}: {dg[k]:.6e} {do[k]:.6e} {rel[k]:.1e}")
     assert (rel[:10] <= 1e-9).all(), rel[:10]
     assert np.all(np.isfinite(dg)) and np.all(dg > 0)
+
+
+# ------------------------------------------------------------------ diagnostics
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diagnostics_match_moments(mx, precision):
+    """Field sums, min sigma and the sigma / positivity counts of
+    mxe_get_diagnostics against the same quantities formed in numpy from
+    mxe_get_moments; two calls return bitwise the same (fixed summation
+    order), on a grid of several diagnostic blocks with a ragged tail."""
+    nx, ny = 301, 77
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(nx, ny, setup)
+    s = jets_gpu_solver(mx, nx, ny, setup, precision=precision)
+    s.set_state(aos_to_soa(prim))
+    s.step(5, float("inf"))
+    d1, d2 = s.diagnostics(), s.diagnostics()
+    assert d1 == d2
+    U = s.get_moments("conserved")
+    sig = s.get_moments("sigma")
+    for k in range(14):
+        ref = math.fsum(U[k].ravel())
+        assert abs(d1["sums"][k] - ref) <= 1e-12 * max(np.abs(U[k]).sum(), 1e-300)
+    assert d1["min_sigma"] == sig.min()
+    assert d1["n_sigma_below_lim"] == int((sig < 1e-4).sum())
+    assert d1["n_sigma_above_one"] == int((sig > 1.0).sum())
+    assert d1["n_nonfinite"] == 0 and d1["n_nonpositive"] == 0
