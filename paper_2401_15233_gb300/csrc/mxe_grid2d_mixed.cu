@@ -313,6 +313,18 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
             for (int k = 0; k < NF; ++k) Fy[k * NTm + tid] = F[k];
         }
     }
+    // final stage without the shared-memory prefetch: load this cell's U^n
+    // and W^n now, so that their latency overlaps the barrier and the
+    // source and flux-difference arithmetic below
+    double Ureg[PF ? 1 : NF];
+    float Wreg[PF ? 1 : NF];
+    if (!PF && a.final_stage && inside) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            Ureg[k] = a.Ubase[o + PH::ufield(k) * g.fstride];
+            Wreg[k] = a.Wbase[o + k * g.fstride];
+        }
+    }
     asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
 
@@ -349,11 +361,11 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
                 bool bad = false;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
-                    double ub = PF ? Upf[k * PF + tid] : a.Ubase[o + PH::ufield(k) * g.fstride];
+                    double ub = PF ? Upf[k * PF + tid] : Ureg[k];
                     double un = ub + (double)dU[k];
                     a.Uout[o + PH::ufield(k) * g.fstride] = un;
                     bad |= !isfinite(un);
-                    Wc[k] = PF ? Wpf[k * PF + tid] : a.Wbase[o + k * g.fstride];
+                    Wc[k] = PF ? Wpf[k * PF + tid] : Wreg[k];
                 }
                 PH::increment(Wc, dU, Wn);
 #pragma unroll
