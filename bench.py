@@ -41,6 +41,15 @@ UNIT = "cell-updates/s"
 #   jets): ten fields instead of fourteen -> fp64 400 B, mixed 360 B
 BYTES_PER_CELL_UPDATE = {("fp64", False): 560.0, ("mixed", False): 504.0,
                          ("fp64", True): 400.0, ("mixed", True): 360.0}
+# DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over the two stage launches of one step, 2048^2
+# crossed jets, 4.19e6 cells; scaled to the benchmark grid by cell count)
+TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 341.1}
+# Issue-rate roofline of the mixed planar stage kernel (it is bound by
+# instruction issue, not by DRAM): thread instructions per cell-update over
+# both stages (ncu smsp__inst_executed.sum x 32 / cells, 1024^2 crossed
+# jets) against 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
+THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 6714.0}
 KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed",
           ("fp64", True): "mxe_stage14_2d_f64_planar", ("mixed", True): "mxe_stage14_2d_mixed_planar_b3"}
 
@@ -83,6 +92,20 @@ def finite_json(x):
     if isinstance(x, (list, tuple)):
         return [finite_json(v) for v in x]
     return x
+
+
+def issue_roofline(precision, planar, ncell, step_s, clk):
+    """Achieved thread-instruction issue rate of one step of the stage
+    kernel against the scheduler peak at the sampled SM clock."""
+    per = THREAD_INST_PER_CELL_UPDATE.get((precision, planar))
+    if per is None:
+        return None
+    mhz = (clk.summary() or {}).get("sm_mhz") if clk else None
+    mhz = mhz or 2070.0
+    peak = 152 * 4 * 32 * mhz * 1e6 / 1e12
+    ach = per * ncell / step_s / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
+            "thread_inst_per_cell_update": per, "peak_from": "152 SMs x 4 x 32 lanes x sm_mhz"}
 
 
 def peaks():
@@ -516,9 +539,12 @@ def main():
                    "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
                    "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": (TRAFFIC_PER_CELL_UPDATE[(args.precision, planar)] * ncell
+                                 if (args.precision, planar) in TRAFFIC_PER_CELL_UPDATE else None),
                      "kernel": KERNEL[(args.precision, planar)], "peak_source": src,
                      "bytes_per_cell_update": bpc},
+        "roofline_issue": issue_roofline(args.precision, planar, ncell, kt, clk),
         "compare": {"precision": other, "value": other_value, "unit": UNIT, "steps": csteps,
                     "ms_per_step": total2 / csteps, "speedup_of_headline": value / other_value,
                     "roofline": {"bound": "hbm", "achieved": ach2, "peak": hbm, "unit": "GB/s",
