@@ -24,6 +24,7 @@ FLUX_HLL, FLUX_RUSANOV = 0, 1
 LIM_MINMOD, LIM_VANALBADA = 0, 1
 TAU_NONE, TAU_CONST, TAU_HARDSPHERE = 0, 1, 2
 FE, RK2 = 0, 1
+SRC_EXPLICIT, SRC_POINT_IMPLICIT = 0, 1
 MAX_SPANS = 4
 MARGIN = 4
 
@@ -74,6 +75,7 @@ class Cfg(C.Structure):
         ("tau_model", C.c_int),
         ("tau_ref", C.c_double), ("rho_ref", C.c_double), ("T_ref", C.c_double),
         ("side", Side * 4),
+        ("source_scheme", C.c_int),
     ]
 
 
@@ -229,14 +231,17 @@ def source(Q, tau):
 def make_cfg(system=14, nx=64, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, order=2,
              integrator=RK2, flux=FLUX_HLL, limiter=LIM_MINMOD, cfl=0.5,
              sigma_lim=1e-4, k_ws=1.0, tau_model=TAU_NONE, tau_ref=1.0, rho_ref=1.0,
-             T_ref=1.0, sides=None) -> Cfg:
-    """sides: list of 4 dicts {type, state (prim), spans: [(lo, hi, prim), ...]}."""
+             T_ref=1.0, sides=None, source_scheme=0) -> Cfg:
+    """sides: list of 4 dicts {type, state (prim), spans: [(lo, hi, prim), ...]};
+    source_scheme: SRC_EXPLICIT (BGK source in the stage residual) or
+    SRC_POINT_IMPLICIT (backward-Euler relaxation after each stage)."""
     c = Cfg()
     c.system, c.nx, c.ny = system, nx, ny
     c.x0, c.x1, c.y0, c.y1 = x0, x1, y0, y1
     c.order, c.integrator, c.flux, c.limiter = order, integrator, flux, limiter
     c.cfl, c.sigma_lim, c.k_ws = cfl, sigma_lim, k_ws
     c.tau_model, c.tau_ref, c.rho_ref, c.T_ref = tau_model, tau_ref, rho_ref, T_ref
+    c.source_scheme = source_scheme
     sides = sides or [{} for _ in range(4)]
     for s, sd in enumerate(sides):
         c.side[s].base_type = sd.get("type", BC_TRANSMISSIVE)
@@ -348,6 +353,7 @@ class CfgT(C.Structure):
         ("tau_model", C.c_int),
         ("tau_ref", _D2), ("rho_ref", _D2), ("T_ref", _D2),
         ("side", SideT * 4),
+        ("source_scheme", C.c_int),
     ]
 
 
@@ -376,7 +382,7 @@ def tangent_cfg(cfg: Cfg, d_states=None, d_tau_ref=0.0, d_rho_ref=0.0, d_T_ref=0
     relaxation parameters."""
     t = CfgT()
     for name in ("system", "nx", "ny", "x0", "x1", "y0", "y1", "order", "integrator", "flux",
-                 "limiter", "cfl", "sigma_lim", "k_ws", "tau_model"):
+                 "limiter", "cfl", "sigma_lim", "k_ws", "tau_model", "source_scheme"):
         setattr(t, name, getattr(cfg, name))
     for name, dv in (("tau_ref", d_tau_ref), ("rho_ref", d_rho_ref), ("T_ref", d_T_ref)):
         getattr(t, name)[0] = getattr(cfg, name)

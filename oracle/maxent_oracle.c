@@ -563,6 +563,44 @@ static void source(const or_cfg *c, const real *Q, real *C) {
     if (c->system == 5) or5_source(Q, tau, C); else or14_source(Q, tau, C);
 }
 
+/* Primitive moments of the Maxwellian with the density, velocity and
+ * pressure of Q: 5-moment (rho, u, P, 0, 3 P^2/rho); 14-moment
+ * (rho, u, p delta_ij, 0, 15 p^2/rho), p = tr P / 3 (Sec. 2.3, 2.4: the
+ * equilibrium moments the BGK source relaxes towards). */
+static void maxwellian_prim(const or_cfg *c, const real *Q, real *QM) {
+    if (c->system == 5) {
+        QM[0] = Q[0]; QM[1] = Q[1]; QM[2] = Q[2]; QM[3] = 0.0;
+        QM[4] = 3.0 * Q[2] * Q[2] / Q[0];
+        return;
+    }
+    real p = (Q[4] + Q[7] + Q[9]) / 3.0;
+    for (int k = 0; k < 14; ++k) QM[k] = 0.0;
+    QM[0] = Q[0]; QM[1] = Q[1]; QM[2] = Q[2]; QM[3] = Q[3];
+    QM[4] = p; QM[7] = p; QM[9] = p;
+    QM[13] = 15.0 * p * p / Q[0];
+}
+
+/* Point-implicit BGK source over h (reading of the remark closing the
+ * cost discussion of Sec. 4.3: below Kn ~ 1e-4 the source limits an
+ * explicit step and a simple point-implicit treatment suffices).  After an
+ * explicit stage V = U_base + h (-div F), solve dU/dt = -(U - U_M)/tau by
+ * backward Euler over h.  The source leaves density, momentum and energy
+ * unchanged, so U_M (the Maxwellian's conserved moments) and tau are V's,
+ * and the implicit step is U = U_M + (V - U_M) / (1 + h/tau).  Density and
+ * momentum are kept as they are (collision invariants). */
+static void relax_cell(const or_cfg *c, real *U, real h) {
+    if (c->tau_model == OR_TAU_NONE) return;
+    int nf = nfields(c);
+    real Q[14], QM[14], UM[14];
+    cons2prim(c, U, Q);
+    real tau = or_tau(c, Q);
+    maxwellian_prim(c, Q, QM);
+    prim2cons(c, QM, UM);
+    real g = 1.0 / (1.0 + h / tau);
+    int first = (c->system == 5) ? 2 : 4;
+    for (int k = first; k < nf; ++k) U[k] = UM[k] + g * (U[k] - UM[k]);
+}
+
 /* HLL with Davis speeds S_L = min(lmin_L, lmin_R), S_R = max(lmax_L, lmax_R)
  * (reading: the paper names HLL, Sec. 3.1; the formula is the textbook one),
  * or Rusanov with s = max |lambda| over both states. */
@@ -745,7 +783,11 @@ static void residual_region(const or_cfg *c, const blk *b, real *A,
         for (int i = xa; i < xb; ++i) {
             real *Lc = L + ((size_t)(j - ya) * rw + (i - xa)) * nf;
             real C[14];
-            source(c, cell(b, Qp, i, j), C);
+            if (c->source_scheme == OR_SRC_POINT_IMPLICIT) {
+                for (int k = 0; k < nf; ++k) C[k] = 0.0;
+            } else {
+                source(c, cell(b, Qp, i, j), C);
+            }
             for (int k = 0; k < nf; ++k) Lc[k] = C[k];
         }
     int ndim = (c->ny == 1) ? 1 : 2;
@@ -821,7 +863,9 @@ int or_block_residual(const or_cfg *c, int i0, int j0, int w, int h,
 
 /* One step (forward Euler or midpoint RK2, Sec. 3):
  *   FE : U^{n+1} = U^n + dt L(U^n)
- *   RK2: U*      = U^n + dt/2 L(U^n),  U^{n+1} = U^n + dt L(U*)   */
+ *   RK2: U*      = U^n + dt/2 L(U^n),  U^{n+1} = U^n + dt L(U*)
+ * With the point-implicit source, L is -div F and every stage result is
+ * relaxed over its own step (dt, or dt/2 for U*) by relax_cell. */
 int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
                   const real *Ub, real dt, real *Uout) {
     blk b;
@@ -840,6 +884,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
                 real *Lc = L + ((size_t)j * w + i) * nf;
                 real *Uo = Uout + ((size_t)j * w + i) * nf;
                 for (int k = 0; k < nf; ++k) Uo[k] = Uc[k] + dt * Lc[k];
+                if (c->source_scheme == OR_SRC_POINT_IMPLICIT) relax_cell(c, Uo, dt);
             }
         free(L);
         free(A);
@@ -865,6 +910,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
             real *Sc = cell(&b, S, i, j);
             real *Lc = L + ((size_t)(j - ya) * rw + (i - xa)) * nf;
             for (int k = 0; k < nf; ++k) Sc[k] = Uc[k] + 0.5 * dt * Lc[k];
+            if (c->source_scheme == OR_SRC_POINT_IMPLICIT) relax_cell(c, Sc, 0.5 * dt);
         }
     fill_bc(c, &b, S);
     real *L2 = (real *)malloc((size_t)w * h * nf * sizeof(real));
@@ -875,6 +921,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
             real *Lc = L2 + ((size_t)j * w + i) * nf;
             real *Uo = Uout + ((size_t)j * w + i) * nf;
             for (int k = 0; k < nf; ++k) Uo[k] = Uc[k] + dt * Lc[k];
+            if (c->source_scheme == OR_SRC_POINT_IMPLICIT) relax_cell(c, Uo, dt);
         }
     free(L2);
     free(S);

@@ -83,6 +83,7 @@ enum { OR_FLUX_HLL = 0, OR_FLUX_RUSANOV = 1 };
 enum { OR_LIM_MINMOD = 0, OR_LIM_VANALBADA = 1 };
 enum { OR_TAU_NONE = 0, OR_TAU_CONST = 1, OR_TAU_HARDSPHERE = 2 };
 enum { OR_FE = 0, OR_RK2 = 1 };
+enum { OR_SRC_EXPLICIT = 0, OR_SRC_POINT_IMPLICIT = 1 };
 #define OR_MAX_SPANS 4
 
 typedef struct {
@@ -105,6 +106,8 @@ typedef struct {
     int    tau_model;     /* OR_TAU_*                                      */
     or_real tau_ref, rho_ref, T_ref;
     or_side side[4];      /* 0 xlo, 1 xhi, 2 ylo, 3 yhi                    */
+    int    source_scheme; /* OR_SRC_*: BGK source explicit in the stage or
+                             point-implicit after it                       */
 } or_cfg;
 
 /* A block is a rectangle of cells [i0, i0+w) x [j0, j0+h) of the global
@@ -127,7 +130,8 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
                   const double *Ub, double dt, double *Uout);
 
 /* Residual L(U) = -div F + C on the interior of a block whose BC sides are
- * filled here; margins as in or_block_step. Lout is w*h*nf. */
+ * filled here; margins as in or_block_step. Lout is w*h*nf.  With the
+ * point-implicit source the residual is the explicit part -div F. */
 int or_block_residual(const or_cfg *c, int i0, int j0, int w, int h,
                       const double *Ub, double *Lout);
 
