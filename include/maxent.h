@@ -62,6 +62,7 @@ enum { MXE_BC_TRANSMISSIVE = 0, MXE_BC_PERIODIC = 1, MXE_BC_DIRICHLET = 2 };
 enum { MXE_SIDE_XLO = 0, MXE_SIDE_XHI = 1, MXE_SIDE_YLO = 2, MXE_SIDE_YHI = 3 };
 enum { MXE_TAU_NONE = 0, MXE_TAU_CONST = 1, MXE_TAU_HARDSPHERE = 2 };
 enum { MXE_PRIMITIVE = 0, MXE_CONSERVED = 1, MXE_SIGMA = 2, MXE_CONSERVED_RESTORE = 3 };
+enum { MXE_SOURCE_EXPLICIT = 0, MXE_SOURCE_POINT_IMPLICIT = 1 };
 
 typedef struct {
     int    system;       /* 5 (1D1V, Sec. 2.3) or 14 (3D3V, Sec. 2.4)            */
@@ -152,6 +153,21 @@ mxe_status mxe_set_bc(mxe_ctx *ctx, int side, int type, double lo, double hi,
  *              this is lambda/v_th with lambda proportional to 1/rho. */
 mxe_status mxe_set_relaxation(mxe_ctx *ctx, int model, double tau_ref, double rho_ref,
                               double T_ref);
+
+/* How the BGK source enters a stage (the closing remark of Sec. 4.3: once
+ * the source limits an explicit step, below Kn ~ 1e-4, a simple
+ * point-implicit treatment suffices).  MXE_SOURCE_EXPLICIT (default): the
+ * source is part of the stage residual.  MXE_SOURCE_POINT_IMPLICIT: the
+ * stage advances the flux divergence only, V = U_base + h (-div F) with h
+ * the stage's step (dt/2 for the RK2 midpoint stage, dt otherwise), and
+ * then solves dU/dt = -(U - U_M)/tau by backward Euler over h; the source
+ * keeps density, momentum and energy, so the Maxwellian U_M and tau are V's
+ * and U = U_M + (V - U_M)/(1 + h/tau) in closed form (density and momentum
+ * are kept as they are).  The CFL step is unchanged (it never included the
+ * source).  Applies to every tube of a batch.  MXE_EINVAL for another
+ * value.  The adjoint entry points return MXE_ESTATE on a context with the
+ * point-implicit source. */
+mxe_status mxe_set_source_scheme(mxe_ctx *ctx, int scheme);
 
 /* March until t_end or max_steps steps, with dt = min(cfl/max_rate, t_end-t)
  * recomputed every step on the device.  t_out / steps_out (may be NULL)

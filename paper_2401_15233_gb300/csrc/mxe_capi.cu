@@ -656,7 +656,7 @@ extern "C" mxe_status mxe_set_relaxation(mxe_ctx* c, int model, double tau_ref, 
     if (model != 0 && !(tau_ref > 0.0)) return fail(c, MXE_EINVAL, "tau_ref must be > 0");
     if (model == 2 && !(rho_ref > 0.0 && T_ref > 0.0))
         return fail(c, MXE_EINVAL, "rho_ref and T_ref must be > 0");
-    c->rp = RelaxParams{model, tau_ref, rho_ref, T_ref};
+    c->rp = RelaxParams{model, tau_ref, rho_ref, T_ref, c->rp.implicit};
     ++c->gen;
     if (c->tubes) {
         for (auto& td : c->tdesc) td.rp = c->rp;
@@ -674,10 +674,25 @@ extern "C" mxe_status mxe_batch_set_relaxation(mxe_ctx* c, int tube, int model, 
     if (tube < 0 || tube >= c->ntubes) return fail(c, MXE_EINVAL, "bad tube %d", tube);
     if (model < 0 || model > 2) return fail(c, MXE_EINVAL, "bad relaxation model %d", model);
     if (model != 0 && !(tau_ref > 0.0)) return fail(c, MXE_EINVAL, "tau_ref must be > 0");
-    c->tdesc[tube].rp = RelaxParams{model, tau_ref, rho_ref, T_ref};
+    c->tdesc[tube].rp = RelaxParams{model, tau_ref, rho_ref, T_ref, c->rp.implicit};
     CK(cudaMemcpyAsync(c->tdesc_d + tube, &c->tdesc[tube], sizeof(TubeDesc),
                        cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_source_scheme(mxe_ctx* c, int scheme) {
+    if (!c) return MXE_EINVAL;
+    if (scheme != MXE_SOURCE_EXPLICIT && scheme != MXE_SOURCE_POINT_IMPLICIT)
+        return fail(c, MXE_EINVAL, "bad source scheme %d", scheme);
+    c->rp.implicit = scheme;
+    ++c->gen;
+    if (c->tubes) {
+        for (auto& td : c->tdesc) td.rp.implicit = scheme;
+        CK(cudaMemcpyAsync(c->tdesc_d, c->tdesc.data(), sizeof(TubeDesc) * c->ntubes,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return MXE_OK;
 }
 
@@ -1257,6 +1272,8 @@ static mxe_status adjoint_ready(mxe_ctx* c) {
     if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
     if (!use_planar(c))
         return fail(c, MXE_ESTATE, "the adjoint needs a planar state (u_z, P_xz, P_yz, q_z zero)");
+    if (c->rp.implicit)
+        return fail(c, MXE_ESTATE, "the adjoint covers the explicit BGK source only");
     mxe_status s = periodic_ok(c);
     if (s != MXE_OK) return s;
     const long long fs = c->g.fstride;

@@ -248,7 +248,7 @@ __device__ __forceinline__ void stage_f64(const Stage2DArgs& a) {
         double Qc[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) Qc[k] = W[k * NBOX + (cy + 2) * BX + cx + 2];
-        if (p.tau_model != 0) {
+        if (p.tau_model != 0 && !p.src_implicit) {
             PH::source(Qc, PH::tau(p, Qc), L);
         } else {
 #pragma unroll
@@ -282,10 +282,16 @@ __device__ __forceinline__ void stage_f64(const Stage2DArgs& a) {
             bool bad = false;
             double cdt = mul_rn(a.coef, dt);
 #pragma unroll
+            for (int k = 0; k < NF; ++k)
+                Un[k] = add_rn(a.Ubase[o + PH::ufield(k) * g.fstride], mul_rn(cdt, L[k]));
+            if (p.tau_model != 0 && p.src_implicit) {   // point-implicit source over cdt
+                double Qv[NF];
+                PH::cons2prim_rn(Un, Qv);
+                PH::relax_cons(Un, Qv, PH::tau(p, Qv), cdt);
+            }
+#pragma unroll
             for (int k = 0; k < NF; ++k) {
-                long long ok = o + PH::ufield(k) * g.fstride;
-                Un[k] = add_rn(a.Ubase[ok], mul_rn(cdt, L[k]));
-                a.Uout[ok] = Un[k];
+                a.Uout[o + PH::ufield(k) * g.fstride] = Un[k];
                 bad |= !isfinite(Un[k]);
             }
             if (a.final_stage) {

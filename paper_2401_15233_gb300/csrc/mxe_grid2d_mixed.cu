@@ -334,7 +334,7 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
         float Qc[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) Qc[k] = W[k * NBOXm + (cy + 2) * BXm + cx + 2];
-        if (p.tau_model != 0) {
+        if (p.tau_model != 0 && !p.src_implicit) {
             PH::source(Qc, PH::tau(p, Qc), L);
         } else {
 #pragma unroll
@@ -350,24 +350,37 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
             float dU[NF], Wc[NF], Wn[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) dU[k] = cdt * L[k];
+            const bool implicit = p.tau_model != 0 && p.src_implicit;
             if (!a.final_stage) {
                 // W* = prim(U^n + dt/2 L): base primitives are this cell's W^n (= stencil)
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Wc[k] = W[k * NBOXm + (cy + 2) * BXm + cx + 2];
                 PH::increment(Wc, dU, Wn);
+                if (implicit) {      // point-implicit source over cdt
+                    float N[NF];
+                    PH::relax_prim(Wn, 1.0f / (1.0f + cdt / PH::tau(p, Wn)), N);
+                }
 #pragma unroll
                 for (int k = 0; k < NF; ++k) a.Wout[o + k * g.fstride] = Wn[k];
             } else {
                 bool bad = false;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) Wc[k] = PF ? Wpf[k * PF + tid] : Wreg[k];
+                PH::increment(Wc, dU, Wn);
+                if (implicit) {      // relax W, and U by (g - 1)(U - U_M)
+                    float N[NF];
+                    float gm = 1.0f / (1.0f + cdt / PH::tau(p, Wn));
+                    PH::relax_prim(Wn, gm, N);
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) dU[k] += (gm - 1.0f) * N[k];
+                }
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
                     double ub = PF ? Upf[k * PF + tid] : Ureg[k];
                     double un = ub + (double)dU[k];
                     a.Uout[o + PH::ufield(k) * g.fstride] = un;
                     bad |= !isfinite(un);
-                    Wc[k] = PF ? Wpf[k * PF + tid] : Wreg[k];
                 }
-                PH::increment(Wc, dU, Wn);
 #pragma unroll
                 for (int k = 0; k < NF; ++k) a.Wout[o + k * g.fstride] = Wn[k];
                 if (PH::nonpositive(Wn)) atomicOr(&a.clk->status, ST_NONPOSITIVE);

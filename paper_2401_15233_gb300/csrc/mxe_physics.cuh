@@ -58,6 +58,7 @@ struct SchemeParams {
 struct RelaxParams {
     int    model;        // 0 none, 1 const, 2 hard-sphere-like
     double tau_ref, rho_ref, T_ref;
+    int    implicit;     // 1: point-implicit source (relax after each stage)
 };
 
 // sigma_bar = min(max(sigma, sigma_lim), 1)   (Appendix A; upper clamp: reading)
@@ -699,6 +700,53 @@ __device__ __forceinline__ T tau_of(const RelaxParams& rp, const T* Q, int syste
     if (rp.model == 1) return T(rp.tau_ref);
     T Tt = system == 5 ? Q[2] / Q[0] : (Q[4] + Q[7] + Q[9]) / (T(3) * Q[0]);
     return T(rp.tau_ref) * (T(rp.rho_ref) / Q[0]) * M<T>::sqrt_(T(rp.T_ref) / Tt);
+}
+
+// ---------------------------------------------------------------- point-implicit BGK
+// Point-implicit source (the closing remark of Sec. 4.3): after an explicit
+// stage V = U_base + h (-div F), backward Euler for dU/dt = -(U - U_M)/tau
+// over h.  The source keeps density, momentum and energy, so the Maxwellian
+// U_M (Sec. 2.3 / 2.4: same density, velocity and pressure) and tau are V's
+// and the step is U = U_M + (V - U_M) / (1 + h/tau) for every moment but
+// density and momentum.  Conserved form, FP64 (Q = primitives of U, tau
+// from Q), each operation rounded on its own as in the plain evaluation.
+__device__ __forceinline__ void relax5_cons(double* U, const double* Q, double tau, double h) {
+    double QM[5] = {Q[0], Q[1], Q[2], 0.0, 3.0 * Q[2] * Q[2] / Q[0]};
+    double UM[5];
+    prim2cons5(QM, UM);
+    double g = 1.0 / (1.0 + h / tau);
+#pragma unroll
+    for (int k = 2; k < 5; ++k) U[k] = add_rn(UM[k], mul_rn(g, sub_rn(U[k], UM[k])));
+}
+
+__device__ __forceinline__ void relax14_cons(double* U, const double* Q, double tau, double h) {
+    double p = (Q[4] + Q[7] + Q[9]) / 3.0;
+    double QM[14] = {Q[0], Q[1], Q[2], Q[3], p, 0.0, 0.0, p, 0.0, p, 0.0, 0.0, 0.0,
+                     15.0 * p * p / Q[0]};
+    double UM[14];
+    prim2cons14(QM, UM);
+    double g = 1.0 / (1.0 + h / tau);
+#pragma unroll
+    for (int k = 4; k < 14; ++k) U[k] = add_rn(UM[k], mul_rn(g, sub_rn(U[k], UM[k])));
+}
+
+// The same relaxation in primitive form (FP32 mixed path): rho, u and p are
+// kept, P <- p I + g (P - p I), q <- g q, R <- R_M + g (R - R_M),
+// g = 1 / (1 + h/tau), R_M = 15 p^2 / rho.  N receives U - U_M of the state
+// before relaxing, in conserved form: prim2cons is linear in (rho, P, q, R)
+// at fixed u, so U - U_M = prim2cons(0, u, P - p I, q, R - R_M), evaluated
+// without the cancellation of a difference of conserved vectors.
+template <class T>
+__device__ __forceinline__ void relax14_prim(T* W, T g, T* N) {
+    T p = (W[4] + W[7] + W[9]) / T(3);
+    T RM = T(15) * p * p / W[0];
+    T D[14] = {T(0), W[1], W[2], W[3], W[4] - p, W[5], W[6], W[7] - p, W[8], W[9] - p,
+               W[10], W[11], W[12], W[13] - RM};
+    prim2cons14(D, N);
+    W[4] = p + g * D[4]; W[5] = g * D[5]; W[6] = g * D[6];
+    W[7] = p + g * D[7]; W[8] = g * D[8]; W[9] = p + g * D[9];
+    W[10] = g * D[10]; W[11] = g * D[11]; W[12] = g * D[12];
+    W[13] = RM + g * D[13];
 }
 
 // ---------------------------------------------------------------- limiter

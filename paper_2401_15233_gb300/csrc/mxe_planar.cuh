@@ -293,6 +293,29 @@ __device__ __forceinline__ T tau_p(int model, T tau_ref, T rho_ref, T T_ref, con
     return tau_ref * (rho_ref / Q[0]) * M<T>::sqrt_(T_ref / Tt);
 }
 
+// Point-implicit relaxation (see relax14_cons / relax14_prim) of the
+// compact state: the Maxwellian is (rho, ux, uy, p, 0, p, p, 0, 0, 15 p^2/rho).
+__device__ __forceinline__ void relax_p_cons(double* U, const double* Q, double tau, double h) {
+    double p = (Q[3] + Q[5] + Q[6]) / 3.0;
+    double QM[NP] = {Q[0], Q[1], Q[2], p, 0.0, p, p, 0.0, 0.0, 15.0 * p * p / Q[0]};
+    double UM[NP];
+    prim2cons_p(QM, UM);
+    double g = 1.0 / (1.0 + h / tau);
+#pragma unroll
+    for (int k = 3; k < NP; ++k) U[k] = add_rn(UM[k], mul_rn(g, sub_rn(U[k], UM[k])));
+}
+
+template <class T>
+__device__ __forceinline__ void relax_p_prim(T* W, T g, T* N) {
+    T p = (W[3] + W[5] + W[6]) / T(3);
+    T RM = T(15) * p * p / W[0];
+    T D[NP] = {T(0), W[1], W[2], W[3] - p, W[4], W[5] - p, W[6] - p, W[7], W[8], W[9] - RM};
+    prim2cons_p(D, N);
+    W[3] = p + g * D[3]; W[4] = g * D[4]; W[5] = p + g * D[5]; W[6] = p + g * D[6];
+    W[7] = g * D[7]; W[8] = g * D[8];
+    W[9] = RM + g * D[9];
+}
+
 // Primitive moments of cons(W) + dU from the increment (see
 // prim_increment14): every term scales with the increment.
 __device__ __forceinline__ void prim_increment_p(const float* W, const float* dU, float* Wn) {

@@ -13,6 +13,7 @@ struct ParamsT {
     int flux, limiter, order;
     int tau_model;
     T tau_ref, rho_ref, T_ref;
+    int src_implicit;           // point-implicit source (relax after each stage)
 };
 
 template <class T>
@@ -27,6 +28,7 @@ __host__ __device__ inline ParamsT<T> make_params(const SchemeParams& sp, const 
     p.tau_ref = T(rp.tau_ref);
     p.rho_ref = T(rp.rho_ref);
     p.T_ref = T(rp.T_ref);
+    p.src_implicit = rp.implicit;
     return p;
 }
 
@@ -79,6 +81,14 @@ struct PhysGeneral {
     static __device__ __forceinline__ void increment(const float* W, const float* dU, float* Wn) {
         prim_increment14(W, dU, Wn);
     }
+    static __device__ __forceinline__ void relax_cons(double* U, const double* Q, double tau,
+                                                      double h) {
+        relax14_cons(U, Q, tau, h);
+    }
+    template <class T>
+    static __device__ __forceinline__ void relax_prim(T* W, T g, T* N) {
+        relax14_prim(W, g, N);
+    }
     template <class T>
     static __device__ __forceinline__ bool nonpositive(const T* Q) {
         return Q[0] <= T(0) || Q[4] <= T(0) || Q[7] <= T(0) || Q[9] <= T(0);
@@ -128,6 +138,14 @@ struct PhysPlanar {
     }
     static __device__ __forceinline__ void increment(const float* W, const float* dU, float* Wn) {
         prim_increment_p(W, dU, Wn);
+    }
+    static __device__ __forceinline__ void relax_cons(double* U, const double* Q, double tau,
+                                                      double h) {
+        relax_p_cons(U, Q, tau, h);
+    }
+    template <class T>
+    static __device__ __forceinline__ void relax_prim(T* W, T g, T* N) {
+        relax_p_prim(W, g, N);
     }
     template <class T>
     static __device__ __forceinline__ bool nonpositive(const T* Q) {

@@ -22,6 +22,9 @@ template <int NF> struct Sys;
 template <> struct Sys<5> {
     static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim5_rn(U, Q); }
     static __device__ __forceinline__ void prim2cons(const double* Q, double* U) { prim2cons5(Q, U); }
+    static __device__ __forceinline__ void relax(double* U, const double* Q, double tau, double h) {
+        relax5_cons(U, Q, tau, h);
+    }
     static __device__ __forceinline__ void eval(const double* Q, const SchemeParams& sp, double* U,
                                                 double* F, double& lo, double& hi) {
         face_eval5(Q, sp, U, F, lo, hi);
@@ -38,6 +41,9 @@ template <> struct Sys<5> {
 template <> struct Sys<14> {
     static __device__ __forceinline__ void cons2prim(const double* U, double* Q) { cons2prim14_rn(U, Q); }
     static __device__ __forceinline__ void prim2cons(const double* Q, double* U) { prim2cons14(Q, U); }
+    static __device__ __forceinline__ void relax(double* U, const double* Q, double tau, double h) {
+        relax14_cons(U, Q, tau, h);
+    }
     static __device__ __forceinline__ void eval(const double* Q, const SchemeParams& sp, double* U,
                                                 double* F, double& lo, double& hi) {
         face_eval14<double, 0>(Q, sp, U, F, lo, hi);
@@ -172,7 +178,7 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
             double Qc[NF], L[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) Qc[k] = W[k * BOX1 + tid + 2];
-            if (td.rp.model != 0) {
+            if (td.rp.model != 0 && !td.rp.implicit) {
                 double tau = tau_of<double>(td.rp, Qc, NF);
                 Sys<NF>::source(Qc, tau, L);
             } else {
@@ -186,6 +192,14 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
             for (int k = 0; k < NF; ++k) {
                 L[k] -= (Fb[k * NT1 + tid + 1] - Fb[k * NT1 + tid]) / td.dx;
                 Un[k] = add_rn(base[(long long)k * n + i], mul_rn(cdt, L[k]));
+            }
+            if (td.rp.model != 0 && td.rp.implicit) {   // point-implicit source over cdt
+                double Qv[NF];
+                Sys<NF>::cons2prim(Un, Qv);
+                Sys<NF>::relax(Un, Qv, tau_of<double>(td.rp, Qv, NF), cdt);
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
                 out[(long long)k * n + i] = Un[k];
                 bad |= !isfinite(Un[k]);
             }

@@ -227,7 +227,8 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
             float Qc[NF], L[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) Qc[k] = Wb[k * BOX + tid + 2];
-            if (p.tau_model != 0) {
+            const bool implicit = p.tau_model != 0 && p.src_implicit;
+            if (p.tau_model != 0 && !implicit) {
                 PH::source(Qc, PH::tau(p, Qc), L);
             } else {
 #pragma unroll
@@ -241,16 +242,16 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
             }
             if (!final) {
                 PH::increment(Qc, dU, Wn);
+                if (implicit) {      // point-implicit source over cdt
+                    float N[NF];
+                    PH::relax_prim(Wn, 1.0f / (1.0f + cdt / PH::tau(p, Wn)), N);
+                }
             } else {
                 bool bad = false;
                 double Un[NF];
 #pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    double* u = v.U + (long long)PH::ufield(k) * n + i;
-                    Un[k] = *u + (double)dU[k];
-                    *u = Un[k];
-                    bad |= !isfinite(Un[k]);
-                }
+                for (int k = 0; k < NF; ++k)
+                    Un[k] = v.U[(long long)PH::ufield(k) * n + i] + (double)dU[k];
                 if (resync) {
                     double Q64[NF];
                     PH::cons2prim_rn(Un, Q64);
@@ -262,6 +263,18 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
                     for (int k = 0; k < NF; ++k)
                         Wc[k] = Wbase ? Wbase[(long long)k * n + i] : Qc[k];
                     PH::increment(Wc, dU, Wn);
+                }
+                if (implicit) {      // relax W, and U by (g - 1)(U - U_M)
+                    float N[NF];
+                    float gm = 1.0f / (1.0f + cdt / PH::tau(p, Wn));
+                    PH::relax_prim(Wn, gm, N);
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) Un[k] += (double)((gm - 1.0f) * N[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    v.U[(long long)PH::ufield(k) * n + i] = Un[k];
+                    bad |= !isfinite(Un[k]);
                 }
                 if (bad) status |= ST_NONFINITE;
                 if (PH::nonpositive(Wn)) status |= ST_NONPOSITIVE;
@@ -367,6 +380,7 @@ __device__ void tubes_mixed_body(const TubeMixedArgs& a, const ParamsT<float>& p
         v.p.tau_ref = (float)td.rp.tau_ref;
         v.p.rho_ref = (float)td.rp.rho_ref;
         v.p.T_ref = (float)td.rp.T_ref;
+        v.p.src_implicit = td.rp.implicit;
         TubeClock* ck = a.clk + b;
         const int n = v.n;
 
