@@ -190,13 +190,14 @@ mxe_status mxe_step_dt(mxe_ctx *ctx, int n, const double *dts);
 mxe_status mxe_set_mixed_policy(mxe_ctx *ctx, double sigma_lo, double sigma_hi,
                                 double det_min, int resync_every);
 
-/* 2D MXE_MIXED only: launch shape of the planar (ten-field) fused stage
- * kernel.  blocks_per_sm = 3 (default): at most 80 registers per thread,
- * three blocks per SM; 2: up to 128 registers per thread, two blocks per
- * SM, and the final stage prefetches its own cells' U^n and W^n into shared
- * memory.  The results do not depend on it (the arithmetic is the same).
- * The general (non-planar) kernel always runs at two blocks per SM.
- * MXE_EINVAL for another value, MXE_ESTATE on another kind of context. */
+/* 2D MXE_MIXED only: launch shape of the fused stage kernels (planar
+ * ten-field and general fourteen-field).  blocks_per_sm = 3 (default): at
+ * most 80 registers per thread, three blocks per SM, the final stage's own
+ * cells prefetched into L2; 2: up to 128 registers per thread, two blocks per
+ * SM (planar: the final stage prefetches its own cells' U^n and W^n into
+ * shared memory).  The results do not depend on it (the arithmetic is the
+ * same).  MXE_EINVAL for another value, MXE_ESTATE on another kind of
+ * context. */
 mxe_status mxe_set_stage_occupancy(mxe_ctx *ctx, int blocks_per_sm);
 
 /* Diagnostics of the current state (synchronises). */

@@ -35,6 +35,8 @@ extern "C" __global__ void mxe_stage14_2d_mixed(const Stage2DArgs a, const Param
 extern "C" __global__ void mxe_stage14_2d_mixed_planar(const Stage2DArgs a,
                                                        const ParamsT<float> p,
                                                        const MixedPolicy mp);
+extern "C" __global__ void mxe_stage14_2d_mixed_b3(const Stage2DArgs a, const ParamsT<float> p,
+                                                   const MixedPolicy mp);
 extern "C" __global__ void mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a,
                                                           const ParamsT<float> p,
                                                           const MixedPolicy mp);
@@ -129,7 +131,7 @@ struct mxe_ctx {
     bool mixed = false;
     MixedPolicy mp{0.0f, 0.999f, 1e-3f};
     int resync_every = 16;
-    int stage_occ = 3;                // planar mixed stage kernel: blocks per SM (2 or 3)
+    int stage_occ = 3;                // mixed stage kernels: blocks per SM (2 or 3)
     long long launched = 0;           // steps launched since set_state
     bool state_planar = false;        // z-odd moments exactly zero (and kept so)
     bool w_planar = false;            // layout of W (mixed): compact planar fields
@@ -356,6 +358,10 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
             e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar_b3,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)stage14_2d_mixed_smem(true, 3));
+        if (e == cudaSuccess && c->mixed)
+            e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_b3,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)stage14_2d_mixed_smem(false, 3));
         if (e != cudaSuccess) {
             fail(c, MXE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
             mxe_destroy(c);
@@ -728,10 +734,13 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
     const bool pl = use_planar(c);
     if (c->mixed) {
         if (c->w_planar != pl) launch_resync(c, pl);       // W layout follows the kernel
-        // planar state: three blocks per SM (no prefetch) or two (with the
-        // final-stage prefetch)
+        // three blocks per SM (L2 prefetch) or two (planar: with the final
+        // stage's shared-memory prefetch)
         auto kern_of = [&](bool) {
-            if (!pl) return std::make_pair(mxe_stage14_2d_mixed, stage14_2d_mixed_smem(false, 2));
+            if (!pl)
+                return std::make_pair(c->stage_occ == 3 ? mxe_stage14_2d_mixed_b3
+                                                        : mxe_stage14_2d_mixed,
+                                      stage14_2d_mixed_smem(false, c->stage_occ));
             return c->stage_occ == 3 ? std::make_pair(mxe_stage14_2d_mixed_planar_b3,
                                                       stage14_2d_mixed_smem(true, 3))
                                      : std::make_pair(mxe_stage14_2d_mixed_planar,

@@ -186,12 +186,13 @@ __device__ __forceinline__ double step_dt_m(const DevClock* clk, int slot, doubl
 template <int NF, bool PFON>
 constexpr int prefetch_cells() { return (PFON && NF == NP) ? TXm * TYm : 0; }
 
-// shared memory: own-cell prefetch, stencil box, x and y face fluxes,
-// staged left face states, limiters, reduction scratch
+// shared memory: own-cell prefetch, stencil box, x face fluxes, staged
+// left face states (whose first NF rows then hold the y face fluxes),
+// limiters, reduction scratch
 template <int NF, bool PFON>
 constexpr size_t smem_mixed() {
     return sizeof(double) * (NF * prefetch_cells<NF, PFON>()) +
-           sizeof(float) * (NF * prefetch_cells<NF, PFON>() + NF * NBOXm + 2 * NF * NTm +
+           sizeof(float) * (NF * prefetch_cells<NF, PFON>() + NF * NBOXm + NF * NTm +
                             (2 * NF + 2) * NTm + NPHXm + NPHYm + 8);
 }
 
@@ -216,8 +217,10 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
     float* Wpf = (float*)(Upf + NF * PF);            // [NF][PF] own-cell W^n (final stage)
     float* W = Wpf + NF * PF;                        // [NF][BY][BX]
     float* Fx = W + NF * NBOXm;                      // [NF][256] x-face fluxes
-    float* Fy = Fx + NF * NTm;                       // [NF][256] y-face fluxes
-    float* Ls = Fy + NF * NTm;                       // [2NF+2][256] left face states
+    float* Ls = Fx + NF * NTm;                       // [2NF+2][256] left face states
+    // y-face fluxes: column tid of Ls, written by thread tid once its y face
+    // is done with the staged left state (no other thread uses that column)
+    float* Fy = Ls;
     float* phx = Ls + (2 * NF + 2) * NTm;            // [TY][TX+2]
     float* phy = phx + NPHXm;                        // [TY+2][TX]
     float* red = phy + NPHYm;                        // [8]
@@ -406,6 +409,11 @@ extern "C" __global__ void __launch_bounds__(NTm, 2)
 mxe_stage14_2d_mixed(const Stage2DArgs a, const ParamsT<float> p, const MixedPolicy mp) {
     stage_mixed<PhysGeneral, false>(a, p, mp);
 }
+// general state at three blocks per SM (at most 80 registers)
+extern "C" __global__ void __launch_bounds__(NTm, 3)
+mxe_stage14_2d_mixed_b3(const Stage2DArgs a, const ParamsT<float> p, const MixedPolicy mp) {
+    stage_mixed<PhysGeneral, false>(a, p, mp);
+}
 extern "C" __global__ void __launch_bounds__(NTm, 2)
 mxe_stage14_2d_mixed_planar(const Stage2DArgs a, const ParamsT<float> p, const MixedPolicy mp) {
     stage_mixed<PhysPlanar, true>(a, p, mp);
@@ -418,7 +426,7 @@ mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a, const ParamsT<float> p,
 }
 
 size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm) {
-    if (!planar) return smem_mixed<14, false>();
+    if (!planar) return smem_mixed<14, false>();      // both general variants
     return blocks_per_sm >= 3 ? smem_mixed<NP, false>() : smem_mixed<NP, true>();
 }
 

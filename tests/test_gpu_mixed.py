@@ -184,23 +184,45 @@ def test_mixed_sampled_4096_bench_config(mx, orc):
         assert np.all(np.linalg.norm(got, axis=0)[~ok] == 0)
 
 
-def test_stage_occupancy_same_result(mx):
-    """The planar stage kernel at two blocks per SM (shared-memory prefetch)
-    and at three (80 registers, L2 prefetch) computes the same arithmetic:
-    bitwise equal states and step sizes after 20 steps with a re-sync; the
-    setter rejects other shapes and other contexts."""
+@pytest.mark.parametrize("uz", [0.0, 0.8])
+def test_stage_occupancy_same_result(mx, uz):
+    """The stage kernels at two blocks per SM and at three (80 registers, L2
+    prefetch) run the same source: each variant is bitwise reproducible from
+    run to run, and the two agree bitwise for the planar state.  For the
+    general state the two builds differ in FP32 rounding (the compiler fuses
+    a different set of multiply-add pairs under the two register budgets):
+    after one step they agree within 1e-4 per field measured against the
+    tensor family's size, which is the state's own sensitivity to a 1e-7 data
+    perturbation (measured 1e-4; each build is 1e-4 from the FP64 oracle).
+    The setter rejects other shapes and other contexts."""
     n = 200
     setup = wl.jets_setup(Kn=0.1)
-    prim = aos_to_soa(wl.jets_like_field(n, n, setup))
+    prim = aos_to_soa(wl.jets_like_field(n, n, setup, uz_beam=uz))
     out = {}
-    for occ in (2, 3):
+    for occ in (2, 3, 3):
         s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
         s.set_stage_occupancy(occ)
         s.set_state(prim)
         s.step(20, float("inf"))
-        out[occ] = (s.get_moments("conserved"), s.diagnostics()["t"])
-        assert s.diagnostics()["planar"] == 1
-    assert np.array_equal(out[2][0], out[3][0]) and out[2][1] == out[3][1]
+        res = (s.get_moments("conserved"), s.diagnostics()["t"])
+        if occ in out:
+            assert np.array_equal(res[0], out[occ][0]) and res[1] == out[occ][1]
+        out[occ] = res
+        assert s.diagnostics()["planar"] == int(uz == 0.0)
+    if uz == 0.0:
+        assert np.array_equal(out[2][0], out[3][0]) and out[2][1] == out[3][1]
+    else:
+        one = {}
+        for occ in (2, 3):
+            s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+            s.set_stage_occupancy(occ)
+            s.set_state(prim)
+            s.step(1, float("inf"))
+            one[occ] = s.get_moments("conserved")
+        from tests.test_gpu_implicit import fam_err
+        e = fam_err(soa_to_aos(one[3]), soa_to_aos(one[2]))
+        print("general state, 2 vs 3 blocks per SM, one step:", e.max())
+        assert e.max() <= 1e-4
     with pytest.raises(mx.MaxentError):
         s.set_stage_occupancy(4)
     f = jets_gpu_solver(mx, 16, 16, setup, precision="fp64")
