@@ -44,12 +44,12 @@ BYTES_PER_CELL_UPDATE = {("fp64", False): 560.0, ("mixed", False): 504.0,
 # DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the two stage launches of one step, 2048^2
 # crossed jets, 4.19e6 cells; scaled to the benchmark grid by cell count)
-TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 341.1}
+TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 341.5}
 # Issue-rate roofline of the mixed planar stage kernel (it is bound by
 # instruction issue, not by DRAM): thread instructions per cell-update over
 # both stages (ncu smsp__inst_executed.sum x 32 / cells, 1024^2 crossed
 # jets) against 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
-THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 6714.0}
+THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 6726.0}
 KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed",
           ("fp64", True): "mxe_stage14_2d_f64_planar", ("mixed", True): "mxe_stage14_2d_mixed_planar_b3"}
 
@@ -57,12 +57,12 @@ KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    p.add_argument("--compare-steps", type=int, default=None,
-                   help="timed steps of the other precision (default: --steps)")
+    p.add_argument("--compare-steps", type=int, default=10,
+                   help="timed steps of the other precision")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -118,30 +118,41 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms; only the
+    samples whose timestamps fall inside the timed region (mark_start() ..
+    mark_end()) are summarised."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+        self._summary = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(0.5)
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
+        time.sleep(0.15)
         if self.proc:
             self.proc.terminate()
             try:
@@ -150,18 +161,27 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self._summary is not None:
+            return self._summary
+        import datetime
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        n_all = 0
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
+                if len(f) < 10:
                     continue
                 try:
-                    sm.append(float(f[1])); mx.append(float(f[2]))
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    smv, mxv = float(f[2]), float(f[3])
                 except ValueError:
                     continue
-                for n, v in zip(names, f[5:9]):
+                n_all += 1
+                if self.t0 is not None and not (self.t0 - 0.05 <= ts <= self.t1 + 0.05):
+                    continue
+                sm.append(smv); mx.append(mxv)
+                for n, v in zip(names, f[6:10]):
                     if v.lower() == "active":
                         reasons.add(n)
         except Exception:
@@ -172,9 +192,13 @@ class ClockSampler:
             except Exception:
                 pass
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+            self._summary = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                             "samples_outside_region": n_all}
+        else:
+            self._summary = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                             "reasons": sorted(reasons), "samples": len(sm),
+                             "timed_region_s": self.t1 - self.t0}
+        return self._summary
 
 
 def dist_setup(args, backend=None):
@@ -478,12 +502,15 @@ def main():
         if sampler:
             sampler.__enter__()
         barrier()
+        if sampler:
+            sampler.mark_start()
         ev[0].record(stream)
         for k in range(steps):
             s.step(1, float("inf"), sync=False)
             ev[k + 1].record(stream)
         barrier()
         if sampler:
+            sampler.mark_end()
             sampler.__exit__()
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
@@ -550,7 +577,7 @@ def main():
                     "roofline": {"bound": "hbm", "achieved": ach2, "peak": hbm, "unit": "GB/s",
                                  "frac": ach2 / hbm, "kernel": KERNEL[(other, planar2)],
                                  "bytes_per_cell_update": bpc2}},
-        "gpu_launches": 2 * args.steps + (args.steps // 16 if args.precision == "mixed" else 0),
+        "gpu_launches": 2 * args.steps,
         "e2e": e2e,
         "clocks": clk.summary(),
         "diag": {"t": d["t"], "steps": d["steps"], "min_sigma": d["min_sigma"],

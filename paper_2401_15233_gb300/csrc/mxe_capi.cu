@@ -749,6 +749,7 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
         ParamsT<float> fp = fparams(c);
         a.Ubase = c->U;
         a.Uout = c->U;
+        a.resync = (c->launched + 1) % c->resync_every == 0;
         if (c->cfg.integrator == MXE_RK2) {
             auto k1 = kern_of(false), k2 = kern_of(true);
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
@@ -763,10 +764,7 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
         }
         CK(cudaGetLastError());
         c->slot = (c->slot + 1) % 3;
-        if (++c->launched % c->resync_every == 0) {
-            launch_resync(c, pl);
-            CK(cudaGetLastError());
-        }
+        ++c->launched;
         return MXE_OK;
     }
     auto kern = pl ? mxe_stage14_2d_f64_planar : mxe_stage14_2d_f64;

@@ -11,8 +11,9 @@
 // The primitives of U + dU are formed from the FP32 increment dU with
 // formulas whose terms all scale with dU (prim_increment14 / _p), so the
 // bulk-motion cancellation of a conserved-to-primitive conversion never
-// happens in FP32.  W is re-derived from U in FP64 every few steps
-// (mxe_resync14_2d) so that its FP32 rounding does not accumulate.
+// happens in FP32.  W is re-derived from U in FP64 every few steps (inside
+// the final stage of that step, or by mxe_resync14_2d when the state is set)
+// so that its FP32 rounding does not accumulate.
 // Face states whose closure is ill-conditioned (sigma in [sigma_lim,
 // sig_lo) near the Junk subspace, sigma > sig_hi near the realizability
 // boundary, or det P* < det_min) are re-evaluated in FP64.
@@ -383,6 +384,14 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
                     double un = ub + (double)dU[k];
                     a.Uout[o + PH::ufield(k) * g.fstride] = un;
                     bad |= !isfinite(un);
+                }
+                if (a.resync) {      // the periodic re-sync: W^{n+1} = prim(U^{n+1}) in FP64
+                    double Un[NF], Q64[NF];
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) Un[k] = a.Uout[o + PH::ufield(k) * g.fstride];
+                    PH::cons2prim_rn(Un, Q64);
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) Wn[k] = (float)Q64[k];
                 }
 #pragma unroll
                 for (int k = 0; k < NF; ++k) a.Wout[o + k * g.fstride] = Wn[k];

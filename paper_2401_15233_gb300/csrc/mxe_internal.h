@@ -60,6 +60,7 @@ struct Stage2DArgs {
     double* dt_hist;                // optional: dt of step s at dt_hist[s] (s < dt_hist_cap)
     long long dt_hist_cap;
     int skip_rate;                  // FP64 final stage: no CFL rate (prescribed dt follows)
+    int resync;                     // mixed final stage: W^{n+1} = prim(U^{n+1}) in FP64
 };
 
 // ---- 1D tubes ----
