@@ -389,7 +389,7 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
                     double Un[NF], Q64[NF];
 #pragma unroll
                     for (int k = 0; k < NF; ++k) Un[k] = a.Uout[o + PH::ufield(k) * g.fstride];
-                    PH::cons2prim_rn(Un, Q64);
+                    PH::cons2prim_fast(Un, Q64);
 #pragma unroll
                     for (int k = 0; k < NF; ++k) Wn[k] = (float)Q64[k];
                 }
@@ -449,7 +449,7 @@ __device__ __forceinline__ void resync(const double* U, float* W, const Grid2D& 
     double Uc[PH::NF], Q[PH::NF];
 #pragma unroll
     for (int k = 0; k < PH::NF; ++k) Uc[k] = U[o + PH::ufield(k) * g.fstride];
-    PH::cons2prim_rn(Uc, Q);
+    PH::cons2prim_fast(Uc, Q);
 #pragma unroll
     for (int k = 0; k < PH::NF; ++k) W[o + k * g.fstride] = (float)Q[k];
 }

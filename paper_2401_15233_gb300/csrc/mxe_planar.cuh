@@ -42,6 +42,28 @@ __device__ __forceinline__ void prim2cons_p(const T* Q, T* U) {
     U[9] = rho * u2 * u2 + T(2) * u2 * trP + T(4) * uPu + T(4) * uq + Q[9];
 }
 
+// Primitive recovery with one reciprocal of rho and contractible arithmetic
+// (the FP64 re-sync of the mixed path, whose result is rounded to FP32; each
+// cancelling difference E - m u is one fused operation).
+template <class T>
+__device__ __forceinline__ void cons2prim_p(const T* U, T* Q) {
+    T rho = U[0];
+    T ir = T(1) / rho;
+    T ux = U[1] * ir, uy = U[2] * ir;
+    T Pxx = U[3] - U[1] * ux, Pxy = U[4] - U[1] * uy, Pyy = U[5] - U[2] * uy, Pzz = U[6];
+    T u2 = ux * ux + uy * uy;
+    T trP = Pxx + Pyy + Pzz;
+    T uPx = ux * Pxx + uy * Pxy, uPy = ux * Pxy + uy * Pyy;
+    T uPu = ux * uPx + uy * uPy;
+    T e = rho * u2 + trP;
+    T qx = U[7] - ux * e - T(2) * uPx;
+    T qy = U[8] - uy * e - T(2) * uPy;
+    T uq = ux * qx + uy * qy;
+    Q[0] = rho; Q[1] = ux; Q[2] = uy; Q[3] = Pxx; Q[4] = Pxy; Q[5] = Pyy; Q[6] = Pzz;
+    Q[7] = qx; Q[8] = qy;
+    Q[9] = U[9] - rho * u2 * u2 - T(2) * u2 * trP - T(4) * uPu - T(4) * uq;
+}
+
 // FP64 primitive recovery rounded exactly like the general evaluation order
 // (the vanishing terms it adds are exact zeros).
 __device__ __forceinline__ void cons2prim_p_rn(const double* U, double* Q) {

@@ -38,6 +38,10 @@ struct PhysGeneral {
     static __device__ __forceinline__ void cons2prim_rn(const double* U, double* Q) {
         cons2prim14_rn(U, Q);
     }
+    // fused, one reciprocal (the mixed path's FP64 re-sync)
+    static __device__ __forceinline__ void cons2prim_fast(const double* U, double* Q) {
+        cons2prim14(U, Q);
+    }
     template <class T, int K>
     static __device__ __forceinline__ void face(const T* Q, T sl, T kw, T* U, T* F, T& lo, T& hi) {
         face_eval14<T, K>(Q, sl, kw, U, F, lo, hi);
@@ -100,6 +104,9 @@ struct PhysPlanar {
     static __host__ __device__ constexpr int ufield(int k) { return planar_field(k); }
     static __device__ __forceinline__ void cons2prim_rn(const double* U, double* Q) {
         cons2prim_p_rn(U, Q);
+    }
+    static __device__ __forceinline__ void cons2prim_fast(const double* U, double* Q) {
+        cons2prim_p(U, Q);
     }
     template <class T, int K>
     static __device__ __forceinline__ void face(const T* Q, T sl, T kw, T* U, T* F, T& lo, T& hi) {

@@ -254,7 +254,7 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
                     Un[k] = v.U[(long long)PH::ufield(k) * n + i] + (double)dU[k];
                 if (resync) {
                     double Q64[NF];
-                    PH::cons2prim_rn(Un, Q64);
+                    PH::cons2prim_fast(Un, Q64);
 #pragma unroll
                     for (int k = 0; k < NF; ++k) Wn[k] = (float)Q64[k];
                 } else {
@@ -392,7 +392,7 @@ __device__ void tubes_mixed_body(const TubeMixedArgs& a, const ParamsT<float>& p
                 double Uc[NF], Q[NF];
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uc[k] = v.U[(long long)PH::ufield(k) * n + i];
-                PH::cons2prim_rn(Uc, Q);
+                PH::cons2prim_fast(Uc, Q);
                 float Qf[NF];
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
