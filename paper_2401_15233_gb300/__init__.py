@@ -437,6 +437,8 @@ class Batch(Solver):
     """Independent 1D tubes advanced in one persistent launch."""
 
     def __init__(self, ncells, lengths, **kw):
+        if len(ncells) == 0 or len(ncells) != len(lengths):
+            raise MaxentError(EINVAL, "need one length per tube and at least one tube")
         kw.setdefault("ny", 1)
         kw["nx"] = int(max(ncells))
         self.cfg = make_config(**kw)

@@ -54,7 +54,20 @@ def test_invalid_config_rejected_without_gpu():
     """Validation happens before any device call."""
     import paper_2401_15233_gb300 as mx
     for bad in [dict(system=7), dict(system=5, ny=8), dict(cfl=0.0), dict(order=3),
-                dict(sigma_lim=0.0), dict(k_ws=0.5), dict(nx=2)]:
+                dict(sigma_lim=0.0), dict(k_ws=0.5), dict(nx=2), dict(nx=0), dict(ny=0),
+                dict(nx=-5), dict(nx=3, ny=3)]:
         with pytest.raises(mx.MaxentError) as e:
             mx.Solver(**bad)
         assert e.value.status == mx.EINVAL
+
+
+def test_invalid_batches_rejected_without_gpu():
+    """Empty batches, empty or too short tubes, non-positive lengths and the
+    5-moment mixed batch (mixed precision is 14-moment only)."""
+    import paper_2401_15233_gb300 as mx
+    for ncells, lengths, kw in [([], [], {}), ([0], [1.0], {}), ([100, 2], [1.0, 1.0], {}),
+                                ([100], [0.0], {}), ([100], [-1.0], {}), ([100], [], {}),
+                                ([100], [1.0], dict(system=5, precision="mixed"))]:
+        with pytest.raises(mx.MaxentError) as e:
+            mx.Batch(ncells, lengths, **({"system": 14} | kw))
+        assert e.value.status == mx.EINVAL, (ncells, lengths, kw)
