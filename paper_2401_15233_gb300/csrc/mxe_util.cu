@@ -40,6 +40,35 @@ __device__ __forceinline__ double raw_sigma(const double* Q, int nf) {
     return d.sig;
 }
 
+// sigma <= 1 (with 1e-9 of slack): decided in FP32 where FP32 clearly can
+// (sigma_32 <= 0.99 with every |Q| in [1e-30, 1e30] and det P* >= 1e-3, so
+// that the FP32 error of sigma is orders of magnitude below the 1e-2
+// margin), in FP64 otherwise.  FP64 here runs at 1/64 of the FP32 rate.
+__device__ __forceinline__ bool sigma_within_one(const double* Q, int nf) {
+    bool screen = true;
+    float Qf[14];
+    for (int k = 0; k < nf; ++k) {
+        double a = fabs(Q[k]);
+        screen &= (a == 0.0) || (a >= 1e-30 && a <= 1e30);
+        Qf[k] = (float)Q[k];
+    }
+    if (screen) {
+        float s32;
+        bool cond = true;
+        if (nf == 5) {
+            float th = Qf[2] / Qf[0];
+            s32 = sigma5(Qf[3] / (Qf[0] * th * sqrtf(th)), Qf[4] / (Qf[0] * th * th));
+        } else {
+            Dimless14<float> d;
+            dimless14(Qf, d);
+            s32 = d.sig;
+            cond = d.det >= 1e-3f;
+        }
+        if (cond && s32 <= 0.99f) return true;     // NaN falls through to FP64
+    }
+    return raw_sigma(Q, nf) <= 1.0 + 1e-9;
+}
+
 // 0 ok; 1 non-finite; 2 rho <= 0 or P not positive definite; 3 sigma > 1
 __device__ __forceinline__ int check_prim(const double* Q, int nf) {
     for (int k = 0; k < nf; ++k)
@@ -53,8 +82,7 @@ __device__ __forceinline__ int check_prim(const double* Q, int nf) {
         double det = a * (d * f - e * e) - b * (b * f - e * c) + c * (b * e - d * c);
         if (!(a > 0.0) || !(m2 > 0.0) || !(det > 0.0)) return 2;
     }
-    double s = raw_sigma(Q, nf);
-    if (!(s <= 1.0 + 1e-9)) return 3;
+    if (!sigma_within_one(Q, nf)) return 3;
     return 0;
 }
 
@@ -67,50 +95,91 @@ __device__ __forceinline__ void to_cons(const double* Q, double* U, int nf) {
 
 // Validate a dense input array; the smallest failing cell number and its
 // code go to bad[0], bad[1] (64-bit: code in the top bits).
+// (the field count is a template parameter so that the per-cell arrays stay
+// in registers)
+template <int NF>
+__device__ __forceinline__ void validate_body(const CellMap& m, int kind, const double* src,
+                                              unsigned long long* bad, unsigned* nonplanar) {
+    long long dense, dfs, dev, fs, idx;
+    const bool has = cell_of(m, dense, dfs, dev, fs, idx);
+    bool np = false;
+    if (has) {
+        double V[NF], Q[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) V[k] = src[dense + k * dfs];
+        if (kind == 0) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) Q[k] = V[k];
+        } else {
+            to_prim(V, Q, NF);
+        }
+        int code = check_prim(Q, NF);
+        if (code) atomicMin(bad, ((unsigned long long)idx << 2) | (unsigned long long)code);
+        // planar iff the z-odd moments (u_z, P_xz, P_yz, q_z) vanish; on the
+        // conserved side they are rho u_z, E_xz, E_yz, H_z (same positions)
+        if (NF == 14) np = V[3] != 0.0 || V[6] != 0.0 || V[8] != 0.0 || V[12] != 0.0;
+    }
+    // one atomic per warp that saw a non-planar cell (blocks are whole warps)
+    if (__any_sync(0xffffffffu, np) && (threadIdx.x & 31) == 0) atomicOr(nonplanar, 1u);
+}
+
 extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
                                           unsigned long long* bad, unsigned* nonplanar) {
+    if (nf == 5) validate_body<5>(m, kind, src, bad, nonplanar);
+    else validate_body<14>(m, kind, src, bad, nonplanar);
+}
+
+template <int NF>
+__device__ __forceinline__ void setstate_body(const CellMap& m, int kind, const double* src,
+                                              double* U) {
     long long dense, dfs, dev, fs, idx;
     if (!cell_of(m, dense, dfs, dev, fs, idx)) return;
-    double V[14], Q[14];
-    for (int k = 0; k < nf; ++k) V[k] = src[dense + k * dfs];
-    if (kind == 0) for (int k = 0; k < nf; ++k) Q[k] = V[k];
-    else to_prim(V, Q, nf);
-    int code = check_prim(Q, nf);
-    if (code) atomicMin(bad, ((unsigned long long)idx << 2) | (unsigned long long)code);
-    // planar iff the z-odd moments (u_z, P_xz, P_yz, q_z) vanish; on the
-    // conserved side they are rho u_z, E_xz, E_yz, H_z (same positions)
-    if (nf == 14 && (V[3] != 0.0 || V[6] != 0.0 || V[8] != 0.0 || V[12] != 0.0))
-        atomicOr(nonplanar, 1u);
+    double V[NF], W[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) V[k] = src[dense + k * dfs];
+    if (kind == 0) {
+        to_cons(V, W, NF);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) W[k] = V[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) U[dev + k * fs] = W[k];
 }
 
 extern "C" __global__ void mxe_k_setstate(CellMap m, int nf, int kind, const double* src,
                                           double* U) {
-    long long dense, dfs, dev, fs, idx;
-    if (!cell_of(m, dense, dfs, dev, fs, idx)) return;
-    double V[14], W[14];
-    for (int k = 0; k < nf; ++k) V[k] = src[dense + k * dfs];
-    if (kind == 0) to_cons(V, W, nf);
-    else for (int k = 0; k < nf; ++k) W[k] = V[k];
-    for (int k = 0; k < nf; ++k) U[dev + k * fs] = W[k];
+    if (nf == 5) setstate_body<5>(m, kind, src, U);
+    else setstate_body<14>(m, kind, src, U);
 }
 
 // kind 0 primitive, 1 conserved, 2 raw sigma (one field)
-extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const double* U,
-                                          double* dst) {
+template <int NF>
+__device__ __forceinline__ void getstate_body(const CellMap& m, int kind, const double* U,
+                                              double* dst) {
     long long dense, dfs, dev, fs, idx;
     if (!cell_of(m, dense, dfs, dev, fs, idx)) return;
-    double V[14], Q[14];
-    for (int k = 0; k < nf; ++k) V[k] = U[dev + k * fs];
+    double V[NF], Q[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) V[k] = U[dev + k * fs];
     if (kind == 1) {
-        for (int k = 0; k < nf; ++k) dst[dense + k * dfs] = V[k];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dst[dense + k * dfs] = V[k];
         return;
     }
-    to_prim(V, Q, nf);
+    to_prim(V, Q, NF);
     if (kind == 0) {
-        for (int k = 0; k < nf; ++k) dst[dense + k * dfs] = Q[k];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dst[dense + k * dfs] = Q[k];
         return;
     }
-    dst[idx] = raw_sigma(Q, nf);
+    dst[idx] = raw_sigma(Q, NF);
+}
+
+extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const double* U,
+                                          double* dst) {
+    if (nf == 5) getstate_body<5>(m, kind, U, dst);
+    else getstate_body<14>(m, kind, U, dst);
 }
 
 // Boundary ghost states as the stencil sees them: prim -> conserved -> prim.
@@ -142,8 +211,10 @@ __device__ __forceinline__ double warp_min_d(double v) {
     return v;
 }
 
-extern "C" __global__ void __launch_bounds__(128)
-mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim, double* part) {
+template <int NF>
+__device__ __forceinline__ void diag_body(const CellMap& m, const double* U, double sigma_lim,
+                                          double* part) {
+    constexpr int nf = NF;
     __shared__ double sh[4][DIAG_W];
     double v[DIAG_W];
 #pragma unroll
@@ -151,9 +222,11 @@ mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim, double* part) {
     v[16] = INFINITY;
     long long dense, dfs, dev, fs, idx;
     if (cell_of(m, dense, dfs, dev, fs, idx)) {
-        double V[14], Q[14];
+        double V[NF], Q[NF];
+#pragma unroll
         for (int k = 0; k < nf; ++k) V[k] = U[dev + k * fs];
         bool fin = true;
+#pragma unroll
         for (int k = 0; k < nf; ++k) {
             fin &= isfinite(V[k]);
             v[k] = V[k];
@@ -187,6 +260,12 @@ mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim, double* part) {
         for (int q = 1; q < 4; ++q) r = k == 16 ? fmin(r, sh[q][k]) : r + sh[q][k];
         part[((long long)blockIdx.y * gridDim.x + blockIdx.x) * DIAG_W + k] = r;
     }
+}
+
+extern "C" __global__ void __launch_bounds__(128)
+mxe_k_diag(CellMap m, int nf, const double* U, double sigma_lim, double* part) {
+    if (nf == 5) diag_body<5>(m, U, sigma_lim, part);
+    else diag_body<14>(m, U, sigma_lim, part);
 }
 
 // Pass 2 (one block of 256 threads): acc[k] = the partials combined, each
