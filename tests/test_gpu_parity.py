@@ -491,3 +491,31 @@ def test_diagnostics_match_moments(mx, precision):
     assert d1["n_sigma_below_lim"] == int((sig < 1e-4).sum())
     assert d1["n_sigma_above_one"] == int((sig > 1.0).sum())
     assert d1["n_nonfinite"] == 0 and d1["n_nonpositive"] == 0
+
+
+@pytest.mark.parametrize("target", [0.5, 0.995, 1.0 - 1e-7, 1.0 + 1e-7, 1.0 + 1e-4])
+def test_validation_sigma_boundary(mx, orc, target):
+    """mxe_set_state accepts a state iff its sigma <= 1 (+1e-9): states built
+    with q = 0 and R* = 9 + 2 T2 (1 - sigma) (Eq. sigma-mapping-14mom at q = 0:
+    sigma = A / (2 T2)) at sigma well inside (decided by the FP32 screen),
+    near the boundary (the FP64 path) and just outside, against the oracle's
+    FP64 sigma."""
+    rng = np.random.default_rng(17)
+    Q = wl.random_prim14(rng, 1)[0].copy()
+    Q[10:13] = 0.0
+    p = (Q[4] + Q[7] + Q[9]) / 3.0
+    th = p / Q[0]
+    Ps = np.array([[Q[4], Q[5], Q[6]], [Q[5], Q[7], Q[8]], [Q[6], Q[8], Q[9]]]) / p
+    T2 = float((Ps * Ps).sum())
+    Q[13] = (9.0 + 2.0 * T2 * (1.0 - target)) * Q[0] * th * th
+    s_or = orc.sigma(Q)
+    assert s_or == pytest.approx(target, abs=1e-9)
+    s = mx.Solver(system=14, nx=4, ny=4)
+    field = aos_to_soa(np.broadcast_to(Q, (4, 4, 14)).copy())
+    if s_or <= 1.0 + 1e-9:
+        s.set_state(field)
+        assert s.get_moments("sigma").max() == pytest.approx(s_or, rel=1e-12)
+    else:
+        with pytest.raises(mx.MaxentError) as e:
+            s.set_state(field)
+        assert e.value.status == mx.EUNREALIZABLE
