@@ -422,6 +422,14 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
     return out
 
 
+def workload_config(n, precision, world, planar=True):
+    """The benchmark's workload, as named in both arms' JSON lines."""
+    return {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
+            "n": n, "precision": precision, "flux": "hll", "limiter": "minmod",
+            "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
+            "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"}
+
+
 def run_reference(args, wl):
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
@@ -450,8 +458,7 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"crossed jets 14-moment 2D RK2, oracle sample {n}x{n}",
-                   "n": n, "precision": "fp64", "l2": "inputs larger than L2 not applicable (CPU)"},
+        "config": workload_config(args.n, "fp64 (oracle)", args.gpus),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -561,10 +568,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 (+f64 accumulator, f64 closure islands)",
         "data": "synthetic",
-        "config": {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
-                   "n": n, "precision": args.precision, "flux": "hll", "limiter": "minmod",
-                   "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
-                   "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"},
+        "config": workload_config(n, args.precision, world, planar),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": (TRAFFIC_PER_CELL_UPDATE[(args.precision, planar)] * ncell
