@@ -52,14 +52,6 @@ struct PhysGeneral {
                                                   T& hi, T& sig, T& det) {
         face_eval14<T, K>(Q, sl, kw, U, F, lo, hi, sig, det);
     }
-    // conditioning of the closure at a face state: raw sigma and det P*
-    template <class T>
-    static __device__ __forceinline__ void conditioning(const T* Q, T& sig, T& det) {
-        Dimless14<T> d;
-        dimless14(Q, d);
-        sig = d.sig;
-        det = d.det;
-    }
     template <class T>
     static __device__ __forceinline__ void source(const T* Q, T tau, T* C) { source14(Q, tau, C); }
     template <class T>
@@ -116,13 +108,6 @@ struct PhysPlanar {
     static __device__ __forceinline__ void face_c(const T* Q, T sl, T kw, T* U, T* F, T& lo,
                                                   T& hi, T& sig, T& det) {
         face_eval_p<T, K>(Q, sl, kw, U, F, lo, hi, sig, det);
-    }
-    template <class T>
-    static __device__ __forceinline__ void conditioning(const T* Q, T& sig, T& det) {
-        DimlessP<T> g;
-        dimless_p(Q, g);
-        sig = g.sig;
-        det = g.det;
     }
     template <class T>
     static __device__ __forceinline__ void source(const T* Q, T tau, T* C) { source_p(Q, tau, C); }
