@@ -121,7 +121,10 @@ void      *mxe_get_stream(const mxe_ctx *ctx);
 
 /* Set the state from a SoA array of nf*ny*nx doubles (kind PRIMITIVE or
  * CONSERVED; primitives are converted on the device).  on_device != 0: soa
- * is a device pointer.  Resets t = 0 and the step count.  Every cell is
+ * is a device pointer; otherwise a host pointer: page-locked host memory
+ * (pinned or registered) is read once by the checking kernel itself over the
+ * host link, pageable memory is copied to the device first.  Resets t = 0
+ * and the step count.  Every cell is
  * checked (rho > 0, finite, positive pressure); a failing state returns
  * MXE_EUNREALIZABLE with the first offending cell in the message and
  * leaves the previous state in place.  Kind CONSERVED_RESTORE takes a
@@ -131,7 +134,9 @@ void      *mxe_get_stream(const mxe_ctx *ctx);
 mxe_status mxe_set_state(mxe_ctx *ctx, int kind, const double *soa, int on_device);
 
 /* Read the state into a SoA array (kind PRIMITIVE, CONSERVED; or SIGMA: one
- * field, the raw sigma of Eq. (sigma-mapping-5mom/14mom)).  Synchronises. */
+ * field, the raw sigma of Eq. (sigma-mapping-5mom/14mom)).  A page-locked
+ * host array is written directly by the conversion kernel, a pageable one
+ * through a device copy.  Synchronises. */
 mxe_status mxe_get_moments(mxe_ctx *ctx, int kind, double *soa, int on_device);
 
 /* Boundary condition of one side (Sec. 6: states imposed in two ghost

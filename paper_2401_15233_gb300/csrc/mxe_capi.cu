@@ -62,7 +62,8 @@ int tile_y();
 int tubes_threads();
 
 extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
-                                          unsigned long long* bad, unsigned* nonplanar);
+                                          unsigned long long* bad, unsigned* nonplanar,
+                                          double* copy);
 extern "C" __global__ void mxe_k_setstate(CellMap m, int nf, int kind, const double* src,
                                           double* U);
 extern "C" __global__ void mxe_k_getstate(CellMap m, int nf, int kind, const double* U,
@@ -528,6 +529,18 @@ static mxe_status reset_clock(mxe_ctx* c) {
 }
 
 // ---------------------------------------------------------------- state I/O
+// Device address of a page-locked (pinned or registered) host buffer, which
+// kernels read and write directly over the host link; nullptr for pageable
+// memory (then the data moves through the context's stage buffer).
+static void* pinned_alias(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int on_device) {
     if (!c) return MXE_EINVAL;
     if (!soa) return fail(c, MXE_EINVAL, "soa is NULL");
@@ -537,16 +550,24 @@ extern "C" mxe_status mxe_set_state(mxe_ctx* c, int kind, const double* soa, int
     if (restore) kind = MXE_CONSERVED;
     size_t bytes = sizeof(double) * c->nf * c->ncell;
     const double* src = soa;
+    const double* vsrc = soa;        // what the validation kernel reads
+    double* copy = nullptr;          // where it leaves a device copy
     if (!on_device) {
-        CK(cudaMemcpyAsync(c->stage, soa, bytes, cudaMemcpyHostToDevice, c->stream));
         src = c->stage;
+        vsrc = (const double*)pinned_alias(soa);
+        if (vsrc) {
+            copy = c->stage;         // one pass over the host link, fused with the checks
+        } else {
+            CK(cudaMemcpyAsync(c->stage, soa, bytes, cudaMemcpyHostToDevice, c->stream));
+            vsrc = c->stage;
+        }
     }
     unsigned long long init[2] = {~0ull, 0ull};
     CK(cudaMemcpyAsync(c->scratch, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
     CellMap m = cellmap(c);
     dim3 grid = cellgrid(c, 128);
-    mxe_k_validate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, src, c->scratch,
-                                                (unsigned*)(c->scratch + 1));
+    mxe_k_validate<<<grid, 128, 0, c->stream>>>(m, c->nf, kind, vsrc, c->scratch,
+                                                (unsigned*)(c->scratch + 1), copy);
     CK(cudaGetLastError());
     unsigned long long res[2] = {0, 0};
     CK(cudaMemcpyAsync(res, c->scratch, sizeof res, cudaMemcpyDeviceToHost, c->stream));
@@ -577,11 +598,14 @@ extern "C" mxe_status mxe_get_moments(mxe_ctx* c, int kind, double* soa, int on_
     if (kind < 0 || kind > 2) return fail(c, MXE_EINVAL, "bad kind %d", kind);
     if (!c->have_state) return fail(c, MXE_ESTATE, "no state set");
     int nfo = kind == MXE_SIGMA ? 1 : c->nf;
-    double* dst = on_device ? soa : c->stage;
+    // device array, page-locked host array (written directly by the kernel)
+    // or pageable host array (through the stage buffer)
+    double* pinned = on_device ? nullptr : (double*)pinned_alias(soa);
+    double* dst = on_device ? soa : (pinned ? pinned : c->stage);
     CellMap m = cellmap(c);
     mxe_k_getstate<<<cellgrid(c, 128), 128, 0, c->stream>>>(m, c->nf, kind, c->U, dst);
     CK(cudaGetLastError());
-    if (!on_device)
+    if (!on_device && !pinned)
         CK(cudaMemcpyAsync(soa, c->stage, sizeof(double) * nfo * c->ncell, cudaMemcpyDeviceToHost,
                            c->stream));
     CK(cudaStreamSynchronize(c->stream));

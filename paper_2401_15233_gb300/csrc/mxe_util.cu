@@ -99,7 +99,8 @@ __device__ __forceinline__ void to_cons(const double* Q, double* U, int nf) {
 // in registers)
 template <int NF>
 __device__ __forceinline__ void validate_body(const CellMap& m, int kind, const double* src,
-                                              unsigned long long* bad, unsigned* nonplanar) {
+                                              unsigned long long* bad, unsigned* nonplanar,
+                                              double* copy) {
     long long dense, dfs, dev, fs, idx;
     const bool has = cell_of(m, dense, dfs, dev, fs, idx);
     bool np = false;
@@ -107,6 +108,10 @@ __device__ __forceinline__ void validate_body(const CellMap& m, int kind, const 
         double V[NF], Q[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) V[k] = src[dense + k * dfs];
+        if (copy) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) copy[dense + k * dfs] = V[k];
+        }
         if (kind == 0) {
 #pragma unroll
             for (int k = 0; k < NF; ++k) Q[k] = V[k];
@@ -123,10 +128,13 @@ __device__ __forceinline__ void validate_body(const CellMap& m, int kind, const 
     if (__any_sync(0xffffffffu, np) && (threadIdx.x & 31) == 0) atomicOr(nonplanar, 1u);
 }
 
+// copy (may be null): receives src, same layout (a host-resident src is then
+// read once, over the host link, by this kernel)
 extern "C" __global__ void mxe_k_validate(CellMap m, int nf, int kind, const double* src,
-                                          unsigned long long* bad, unsigned* nonplanar) {
-    if (nf == 5) validate_body<5>(m, kind, src, bad, nonplanar);
-    else validate_body<14>(m, kind, src, bad, nonplanar);
+                                          unsigned long long* bad, unsigned* nonplanar,
+                                          double* copy) {
+    if (nf == 5) validate_body<5>(m, kind, src, bad, nonplanar, copy);
+    else validate_body<14>(m, kind, src, bad, nonplanar, copy);
 }
 
 template <int NF>

@@ -519,3 +519,33 @@ def test_validation_sigma_boundary(mx, orc, target):
         with pytest.raises(mx.MaxentError) as e:
             s.set_state(field)
         assert e.value.status == mx.EUNREALIZABLE
+
+
+def test_pinned_host_buffers(mx, orc):
+    """set_state from page-locked host memory (read by the checking kernel over
+    the host link) and get_moments into it give bitwise what the pageable path
+    gives; a failing pinned input is rejected and leaves the state in place."""
+    import torch
+    n = 37
+    setup = wl.jets_setup(Kn=0.1)
+    prim = aos_to_soa(wl.jets_like_field(n, n + 3, setup))
+    U = aos_to_soa(cons_field(orc, wl.jets_like_field(n, n + 3, setup)))
+    pinned = torch.from_numpy(U.copy()).pin_memory()
+    out_pinned = torch.empty_like(pinned).pin_memory()
+    a = jets_gpu_solver(mx, n, n + 3, setup)
+    b = jets_gpu_solver(mx, n, n + 3, setup)
+    a.set_state(U.copy(), kind="conserved")
+    b.set_state(pinned.numpy(), kind="conserved")
+    a.step(3, 10.0)
+    b.step(3, 10.0)
+    ra = a.get_moments("conserved")
+    b.get_moments("conserved", out=out_pinned.numpy())
+    assert np.array_equal(ra, out_pinned.numpy())
+    bad = pinned.clone().pin_memory()
+    bad[0, 5, 7] = -1.0
+    with pytest.raises(mx.MaxentError) as e:
+        b.set_state(bad.numpy(), kind="conserved")
+    assert e.value.status == mx.EUNREALIZABLE
+    b.get_moments("conserved", out=out_pinned.numpy())
+    assert np.array_equal(ra, out_pinned.numpy())
+    del prim
