@@ -406,7 +406,8 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
         out[prec] = {"forward_ckpt_s": tfc, "backward_s": tb, "ratio": (tfc + tb) / tf,
-                     "backward_over_forward": tb / tf, "grad": [float(x) for x in g]}
+                     "backward_over_forward": tb / tf, "grad": [float(x) for x in g],
+                     "fp64_fallback_segments": getattr(prob, "fp64_fallbacks", 0)}
         del s2, ckpts
     out.update({"t_final": float(dts.sum()), "J": J,
                 "probe_at_background": bool(J == prob.setup["background"][0])})

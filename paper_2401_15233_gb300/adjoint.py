@@ -123,7 +123,10 @@ def forward_checkpointed(prob: JetsProblem, p):
 
 def backward_checkpointed(prob: JetsProblem, s: Solver, ckpts, dts, gJ=1.0):
     """dJ/dp by the reverse sweep, segment by segment (recomputing each
-    segment from its checkpoint)."""
+    segment from its checkpoint).  With the FP32 face-state reverse, a
+    segment whose adjoint leaves the FP32 range (non-finite values) is swept
+    again with the FP64 reverse from the same incoming adjoint; the number of
+    such segments is left in prob.fp64_fallbacks."""
     import torch
     a, b = prob.probe
     ubar = torch.zeros((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
@@ -131,10 +134,22 @@ def backward_checkpointed(prob: JetsProblem, s: Solver, ckpts, dts, gJ=1.0):
     torch.cuda.synchronize()          # written on torch's stream, read on the library's
     G = np.zeros((4, GHOST_SLOTS, 14))
     tb = 0.0
+    mixed = prob.adjoint_precision == "mixed"
+    prob.fp64_fallbacks = 0
     for k in range(len(ckpts) - 1, -1, -1):
         s.set_state(ckpts[k], kind="restore")
         s.adjoint_record(dts[k * prob.ckpt:(k + 1) * prob.ckpt])
+        keep = ubar.clone() if mixed else None
+        torch.cuda.synchronize()
         g, t = s.adjoint_run(ubar)
+        if mixed and not (np.isfinite(g).all() and np.isfinite(t)
+                          and bool(torch.isfinite(ubar).all())):
+            ubar.copy_(keep)
+            torch.cuda.synchronize()
+            s.set_adjoint_precision("fp64")
+            g, t = s.adjoint_run(ubar)
+            s.set_adjoint_precision("mixed")
+            prob.fp64_fallbacks += 1
         G += g
         tb += t
     # imposed states: left slot (side XLO, span 0) moves u_x, bottom (YLO) u_y
