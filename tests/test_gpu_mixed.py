@@ -228,3 +228,40 @@ def test_stage_occupancy_same_result(mx, uz):
     f = jets_gpu_solver(mx, 16, 16, setup, precision="fp64")
     with pytest.raises(mx.MaxentError):
         f.set_stage_occupancy(3)
+
+
+def test_mixed_l1_bench_size_against_fp64(mx):
+    """The bench workload (crossed jets, 4096^2): 20 RK2 steps of the mixed path
+    against the all-FP64 GPU path (per-step parity with the oracle 1e-12,
+    sampled at this size in test_gpu_parity), same step sizes.  Per-field L1
+    error within 10x the FP64 path's own change when every primitive of the
+    initial and inflow states is perturbed by 1e-7 relative."""
+    n, nsteps = 4096, 20
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(4096)
+    prim = aos_to_soa(wl.jets_like_field(n, n, setup))
+    ref = jets_gpu_solver(mx, n, n, setup, precision="fp64")
+    ref.set_state(prim)
+    ref.set_dt_history(nsteps)
+    ref.step(nsteps, float("inf"))
+    dts = ref.dt_history(nsteps)
+    A = ref.get_moments("conserved")
+    del ref
+    pert = lambda x: x * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=np.shape(x)))
+    a = math.sqrt(wl.GAMMA_3D)
+    r1, u1, T1 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    r2, u2, T2 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    setup_p = dict(setup, left=wl.maxwellian14(r1, u1, 0.0, T1),
+                   bottom=wl.maxwellian14(r2, 0.0, u2, T2))
+    p64 = jets_gpu_solver(mx, n, n, setup_p, precision="fp64")
+    p64.set_state(pert(prim))
+    p64.step_dt(dts)
+    sens = l1_rel(soa_to_aos(p64.get_moments("conserved")), soa_to_aos(A))
+    del p64
+    m = jets_gpu_solver(mx, n, n, setup, precision="mixed")
+    m.set_state(prim)
+    m.step_dt(dts)
+    e = l1_rel(soa_to_aos(m.get_moments("conserved")), soa_to_aos(A))
+    print("4096^2, 20 steps: mixed L1", e.max(), "sensitivity", sens.max())
+    nz = np.abs(A).reshape(14, -1).sum(1) > 0
+    assert np.all(e[nz] <= np.maximum(10 * sens[nz], 1e-10)), (e, sens)
