@@ -759,31 +759,23 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
     if (c->mixed) {
         if (c->w_planar != pl) launch_resync(c, pl);       // W layout follows the kernel
         // three blocks per SM (L2 prefetch) or two (planar: with the final
-        // stage's shared-memory prefetch)
-        auto kern_of = [&](bool) {
-            if (!pl)
-                return std::make_pair(c->stage_occ == 3 ? mxe_stage14_2d_mixed_b3
-                                                        : mxe_stage14_2d_mixed,
-                                      stage14_2d_mixed_smem(false, c->stage_occ));
-            return c->stage_occ == 3 ? std::make_pair(mxe_stage14_2d_mixed_planar_b3,
-                                                      stage14_2d_mixed_smem(true, 3))
-                                     : std::make_pair(mxe_stage14_2d_mixed_planar,
-                                                      stage14_2d_mixed_smem(true, 2));
-        };
+        // stage's shared-memory prefetch); the same kernel for both stages
+        const bool b3 = c->stage_occ == 3;
+        const auto kern = pl ? (b3 ? mxe_stage14_2d_mixed_planar_b3 : mxe_stage14_2d_mixed_planar)
+                             : (b3 ? mxe_stage14_2d_mixed_b3 : mxe_stage14_2d_mixed);
+        const size_t smem = stage14_2d_mixed_smem(pl, c->stage_occ);
         ParamsT<float> fp = fparams(c);
         a.Ubase = c->U;
         a.Uout = c->U;
         a.resync = (c->launched + 1) % c->resync_every == 0;
         if (c->cfg.integrator == MXE_RK2) {
-            auto k1 = kern_of(false), k2 = kern_of(true);
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
-            k1.first<<<grid, 256, k1.second, c->stream>>>(a, fp, c->mp);
+            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
             a.Win = c->Ws; a.Wout = c->W; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            k2.first<<<grid, 256, k2.second, c->stream>>>(a, fp, c->mp);
+            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
         } else {
-            auto k2 = kern_of(true);
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            k2.first<<<grid, 256, k2.second, c->stream>>>(a, fp, c->mp);
+            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
             std::swap(c->W, c->Ws);
         }
         CK(cudaGetLastError());
