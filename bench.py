@@ -395,8 +395,11 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
     tf = time.perf_counter() - t0
     del s
     out["forward_s"] = tf
-    for prec in ((only_precision,) if only_precision else ("fp64", "mixed")):
+    legs = ((only_precision, "exact"),) if only_precision else (
+        ("fp64", "exact"), ("mixed", "exact"), ("fp64", "frozen"), ("mixed", "frozen"))
+    for prec, lim in legs:
         prob.adjoint_precision = prec
+        prob.adjoint_limiter = lim
         t0 = time.perf_counter()
         J, ckpts, dts, s2 = ad.forward_checkpointed(prob, p0)
         torch.cuda.synchronize()
@@ -405,7 +408,8 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
         g, _ = ad.backward_checkpointed(prob, s2, ckpts, dts)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
-        out[prec] = {"forward_ckpt_s": tfc, "backward_s": tb, "ratio": (tfc + tb) / tf,
+        out[prec if lim == "exact" else f"{prec}_frozen_limiter"] = {
+                     "forward_ckpt_s": tfc, "backward_s": tb, "ratio": (tfc + tb) / tf,
                      "backward_over_forward": tb / tf, "grad": [float(x) for x in g],
                      "fp64_fallback_segments": getattr(prob, "fp64_fallbacks", 0)}
         del s2, ckpts

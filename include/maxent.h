@@ -297,6 +297,16 @@ mxe_status mxe_adjoint_run(mxe_ctx *ctx, double *ubar, int on_device, double *gb
  * adjoint state and all accumulations stay FP64).  MXE_EINVAL otherwise. */
 mxe_status mxe_set_adjoint_precision(mxe_ctx *ctx, int precision);
 
+/* Linearisation of the shared limiter in the adjoint.  frozen = 0 (default):
+ * the exact derivative of the branch the primal takes, the limiter's
+ * sub-gradient included (what the oracle's tangent computes).  frozen = 1:
+ * the limiter value phi is held constant in the derivative, a common choice
+ * for adjoints of limited schemes: the shared most-stringent limiter is not
+ * differentiable at the scale of finite differences where a field's
+ * differences are near round-off, and its derivative there scales as the
+ * inverse of those differences.  MXE_EINVAL for another value. */
+mxe_status mxe_set_adjoint_limiter(mxe_ctx *ctx, int frozen);
+
 /* Adjoint of the residual L(U) = -div F + C at the conserved state U
  * (dense (14, ny, nx)): out = (dL/dU)^T V, and adds (dL/dg)^T V to gbar
  * and (dL/dtau_ref)^T V to *taubar.  For checking the reverse sweep one

@@ -76,6 +76,7 @@ class Cfg(C.Structure):
         ("tau_ref", C.c_double), ("rho_ref", C.c_double), ("T_ref", C.c_double),
         ("side", Side * 4),
         ("source_scheme", C.c_int),
+        ("frozen_limiter", C.c_int),
     ]
 
 
@@ -354,6 +355,7 @@ class CfgT(C.Structure):
         ("tau_ref", _D2), ("rho_ref", _D2), ("T_ref", _D2),
         ("side", SideT * 4),
         ("source_scheme", C.c_int),
+        ("frozen_limiter", C.c_int),
     ]
 
 
@@ -375,12 +377,15 @@ def tangent_lib():
     return _tlib
 
 
-def tangent_cfg(cfg: Cfg, d_states=None, d_tau_ref=0.0, d_rho_ref=0.0, d_T_ref=0.0) -> CfgT:
+def tangent_cfg(cfg: Cfg, d_states=None, d_tau_ref=0.0, d_rho_ref=0.0, d_T_ref=0.0,
+                frozen_limiter=False) -> CfgT:
     """Dual configuration: cfg's values with derivative directions for the
     imposed boundary states (d_states[s][0] = base state of side s,
     d_states[s][1 + n] = span n; primitive vectors of 14) and the
-    relaxation parameters."""
+    relaxation parameters.  frozen_limiter: the shared limiter phi is held
+    constant in the derivative (its value, hence the primal, unchanged)."""
     t = CfgT()
+    t.frozen_limiter = 1 if frozen_limiter else 0
     for name in ("system", "nx", "ny", "x0", "x1", "y0", "y1", "order", "integrator", "flux",
                  "limiter", "cfl", "sigma_lim", "k_ws", "tau_model", "source_scheme"):
         setattr(t, name, getattr(cfg, name))

@@ -661,6 +661,12 @@ static real shared_phi(const or_cfg *c, const real *Qm, const real *Q0,
     return phi;
 }
 
+/* OR_VALUE(x): x with its derivative dropped (the identity in the plain
+ * build; the derivative build defines it) */
+#ifndef OR_VALUE
+#define OR_VALUE(x) (x)
+#endif
+
 /* face state of cell Q0 on its side sgn (+1 right, -1 left) */
 static void face_state(const or_cfg *c, const real *Qm, const real *Q0,
                        const real *Qp, real sgn, real *Qf) {
@@ -670,6 +676,7 @@ static void face_state(const or_cfg *c, const real *Qm, const real *Q0,
         return;
     }
     real phi = shared_phi(c, Qm, Q0, Qp);
+    if (c->frozen_limiter) phi = OR_VALUE(phi);
     for (int k = 0; k < nf; ++k) {
         /* a field that is flat across the stencil keeps its cell value (its
          * slope phi * 0 vanishes; written out so that its derivative is the

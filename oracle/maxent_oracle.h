@@ -108,6 +108,9 @@ typedef struct {
     or_side side[4];      /* 0 xlo, 1 xhi, 2 ylo, 3 yhi                    */
     int    source_scheme; /* OR_SRC_*: BGK source explicit in the stage or
                              point-implicit after it                       */
+    int    frozen_limiter;/* derivative builds only: the shared limiter phi
+                             is held constant in the derivative (the primal
+                             is unchanged)                                 */
 } or_cfg;
 
 /* A block is a rectangle of cells [i0, i0+w) x [j0, j0+h) of the global

@@ -63,14 +63,18 @@ inline dual pow(const dual& a, double p) {
 }
 inline dual fabs(const dual& a) { return a.v < 0.0 ? -a : a; }
 inline bool isnan(const dual& a) { return a.v != a.v; }
+// the value alone (its derivative dropped)
+inline dual value_of(const dual& a) { return dual(a.v, 0.0); }
 
 }  // namespace ortan
 
 namespace ortan {
 #define OR_REAL ortan::dual
+#define OR_VALUE(x) value_of(x)
 #define OR_TANGENT_BUILD
 #include "maxent_oracle.c"
 #undef OR_TANGENT_BUILD
+#undef OR_VALUE
 #undef OR_REAL
 }  // namespace ortan
 

@@ -26,7 +26,7 @@ __all__ = [
     "mxe_batch_get_clock", "mxe_batch_run", "mxe_set_mixed_policy", "mxe_tube_run_noalloc",
     "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
     "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual", "mxe_set_adjoint_precision",
-    "mxe_set_stage_occupancy", "mxe_set_source_scheme",
+    "mxe_set_stage_occupancy", "mxe_set_source_scheme", "mxe_set_adjoint_limiter",
 ]
 
 SOURCE_EXPLICIT, SOURCE_POINT_IMPLICIT = 0, 1
@@ -120,6 +120,7 @@ def lib():
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
             "mxe_set_stage_occupancy": ([_P, C.c_int], C.c_int),
             "mxe_set_source_scheme": ([_P, C.c_int], C.c_int),
+            "mxe_set_adjoint_limiter": ([_P, C.c_int], C.c_int),
             "mxe_tube_run_noalloc": ([C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_double, _P, C.c_double, C.c_double,
                                       C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int), _P],
@@ -221,6 +222,10 @@ def mxe_last_error(ctx):
 
 def mxe_set_mixed_policy(ctx, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
     _check(ctx, lib().mxe_set_mixed_policy(ctx, sigma_lo, sigma_hi, det_min, resync_every))
+
+
+def mxe_set_adjoint_limiter(ctx, frozen):
+    _check(ctx, lib().mxe_set_adjoint_limiter(ctx, 1 if frozen else 0))
 
 
 def mxe_set_source_scheme(ctx, scheme):
@@ -422,6 +427,11 @@ class Solver:
 
     def set_mixed_policy(self, sigma_lo=0.0, sigma_hi=0.999, det_min=1e-3, resync_every=16):
         mxe_set_mixed_policy(self.ctx, sigma_lo, sigma_hi, det_min, resync_every)
+
+    def set_adjoint_limiter(self, frozen):
+        """False: exact derivative of the limiter branch; True: phi held
+        constant in the adjoint."""
+        mxe_set_adjoint_limiter(self.ctx, frozen)
 
     def set_source_scheme(self, scheme):
         """"explicit" (BGK source in the stage residual) or "point_implicit"

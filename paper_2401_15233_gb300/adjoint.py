@@ -41,7 +41,8 @@ class JetsProblem:
     which the jets blow)."""
 
     def __init__(self, n=512, Kn=0.1, nsteps=500, ckpt=50, probe=32, mach=(3.0, 3.0),
-                 initial="developed", order=2, relax=True, adjoint_precision="fp64"):
+                 initial="developed", order=2, relax=True, adjoint_precision="fp64",
+                 adjoint_limiter="exact"):
         if nsteps % ckpt:
             raise ValueError("nsteps must be a multiple of ckpt")
         if initial not in ("developed", "rest", "smooth"):
@@ -49,6 +50,9 @@ class JetsProblem:
         self.initial_kind = initial
         self.order, self.relax = order, relax
         self.adjoint_precision = adjoint_precision
+        if adjoint_limiter not in ("exact", "frozen"):
+            raise ValueError("adjoint_limiter must be 'exact' or 'frozen'")
+        self.adjoint_limiter = adjoint_limiter
         self.n, self.nsteps, self.ckpt = n, nsteps, ckpt
         self.setup = wl.jets_setup(mach=mach, Kn=Kn)
         self.p0 = (float(mach[0]), float(mach[1]), float(self.setup["tau_ref"]))
@@ -69,6 +73,7 @@ class JetsProblem:
         if self.relax:
             s.set_relaxation(TAU_HARDSPHERE, float(p[2]), su["rho_ref"], su["T_ref"])
         s.set_adjoint_precision(self.adjoint_precision)
+        s.set_adjoint_limiter(self.adjoint_limiter == "frozen")
         return s
 
     def initial(self):

@@ -46,6 +46,7 @@ struct AdjArgs {
                                 //   dphi/ddp, selected field), formed in FP64
     float* LY;                  // [4][ny+2][nx] y limiter of cell j = -1 .. ny
     int f32;                    // contributions Cx, Cy stored as float
+    int frozen_phi;             // the shared limiter held constant in the derivative
     Grid2D g;
     ParamsT<double> p;
 };
@@ -164,6 +165,7 @@ extern "C" __global__ void mxe_adj_limiters(const AdjArgs a) {
     adj::PhiAdj<double> ph{1.0, 0.0, 0.0, -1};
     if (a.p.order == 2) ph = adj::phi_adj<double, NP>(qm, q0, qp, a.p.limiter);
     else ph.phi = 0.0;
+    if (a.frozen_phi) ph.ks = -1;
     float* L = K == 0 ? a.LX : a.LY;
     const float v[4] = {(float)ph.phi, (float)ph.ddm, (float)ph.ddp, (float)ph.ks};
 #pragma unroll
@@ -296,6 +298,7 @@ __device__ __forceinline__ void adj_face_side(const AdjArgs& a, int f, int t, bo
         double Qs[3][NP];
         load_stencil(Qs);
         if (p.order == 2) ph = adj::phi_adj<double, NP>(Qs[0], Qs[1], Qs[2], p.limiter);
+        if (a.frozen_phi) ph.ks = -1;
 #pragma unroll
         for (int k = 0; k < NP; ++k)
             Qf[k] = (T)muscl_face(Qs[0][k], Qs[1][k], Qs[2][k], ph.phi, hs);
@@ -690,10 +693,11 @@ long long adj_f32_floats(const Grid2D& g) {
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      bool f32, float* f32buf, cudaStream_t st) {
+                      bool f32, float* f32buf, bool frozen_phi, cudaStream_t st) {
     AdjArgs a;
     a.U = U; a.V = V; a.coef = coef; a.b1 = b1; a.b2 = b2; a.out = out;
     a.f32 = f32 ? 1 : 0;
+    a.frozen_phi = frozen_phi ? 1 : 0;
     a.Pf = f32buf;
     a.Vf = f32buf + (long long)NP * g.fstride;
     a.DX = a.Vf + (long long)NP * g.fstride;

@@ -52,7 +52,7 @@ const void* tubes_mixed_kernel(bool planar, int nt);
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
-                      bool f32, float* f32buf, cudaStream_t st);
+                      bool f32, float* f32buf, bool frozen_phi, cudaStream_t st);
 long long adj_f32_floats(const Grid2D& g);
 extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g,
                                         int to_pitched);
@@ -121,6 +121,7 @@ struct mxe_ctx {
     double* adjB = nullptr;
     double* adjG = nullptr;           // [4][GHOST_SLOTS][14] imposed-state adjoint, then tau_ref's
     bool adj_f32 = false;             // face-state reverse in FP32 (MXE_MIXED adjoint)
+    bool adj_frozen = false;          // shared limiter held constant in the derivative
     float* adjF = nullptr;            // FP32 per-cell data of that reverse
     // state
     double* U = nullptr;
@@ -1384,14 +1385,17 @@ extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, d
         if (rk2) {
             // U^{n+1} = U^n + dt L(U*): B = dt L'(U*)^T A
             e = adj_stage(un + c->nelem, c->adjA, dt, nullptr, nullptr, c->adjB, c->adjP,
-                          c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
+                          c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF,
+                          c->adj_frozen, c->stream);
             // U* = U^n + dt/2 L(U^n): A = A + B + dt/2 L'(U^n)^T B
             if (e == cudaSuccess)
                 e = adj_stage(un, c->adjB, 0.5 * dt, c->adjA, c->adjB, c->adjA, c->adjP,
-                              c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
+                              c->adjCx, c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF,
+                          c->adj_frozen, c->stream);
         } else {
             e = adj_stage(un, c->adjA, dt, c->adjA, nullptr, c->adjA, c->adjP, c->adjCx,
-                          c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF, c->stream);
+                          c->adjCy, gb, tb, g, p, c->adj_f32, c->adjF,
+                          c->adj_frozen, c->stream);
         }
         if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint stage: %s", cudaGetErrorString(e));
     }
@@ -1442,7 +1446,7 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
     CK(cudaMalloc(&Op, sizeof(double) * c->nelem));
     cudaError_t e = adj_stage(Up, Vp, 1.0, nullptr, nullptr, Op, c->adjP, c->adjCx, c->adjCy,
                               c->adjG, c->adjG + 4 * GHOST_SLOTS * 14, g, p, c->adj_f32,
-                              c->adjF, c->stream);
+                              c->adjF, c->adj_frozen, c->stream);
     if (e == cudaSuccess) {
         double* dst = on_device ? out : tmpU;
         mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0);
@@ -1468,5 +1472,12 @@ extern "C" mxe_status mxe_set_adjoint_precision(mxe_ctx* c, int precision) {
     if (precision != MXE_FP64 && precision != MXE_MIXED)
         return fail(c, MXE_EINVAL, "precision must be MXE_FP64 or MXE_MIXED");
     c->adj_f32 = precision == MXE_MIXED;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_adjoint_limiter(mxe_ctx* c, int frozen) {
+    if (!c) return MXE_EINVAL;
+    if (frozen != 0 && frozen != 1) return fail(c, MXE_EINVAL, "frozen must be 0 or 1");
+    c->adj_frozen = frozen == 1;
     return MXE_OK;
 }
