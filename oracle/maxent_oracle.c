@@ -636,9 +636,53 @@ static void face_flux(const or_cfg *c, const real *QL, const real *QR,
     }
 }
 
+/* Flat-field test of the shared limiter (a reading: the paper states no
+ * tolerance).  Field k of the stencil centred on Q is flat when
+ * m = max(|dm|, |dp|) is within OR_FLAT_TOL times the field's natural scale
+ * at Q, with theta = p / rho and p the mean pressure: rho (density),
+ * sqrt(theta) (velocities), p (pressure tensor), p sqrt(theta) (heat
+ * fluxes), p theta (fourth moment).  The comparisons are multiplied out
+ * (rho, p > 0), with s = P for the 5-moment system and s = tr P = 3p for the
+ * 14-moment one, so that no division or square root enters:
+ *   m <= T rho;  m^2 rho <= T^2 p;  m <= T p;  m^2 rho <= T^2 p^3;
+ *   m rho <= T p^2   (T = OR_FLAT_TOL, p written through s). */
+#define OR_FLAT_TOL 1e-10
+static int field_flat(const or_cfg *c, const real *Q, int k, real m) {
+    real rho = Q[0];
+    int cls;
+    real s, cp, cv, ch, cr;
+    if (c->system == 5) {
+        s = Q[2];
+        cp = OR_FLAT_TOL;
+        cv = OR_FLAT_TOL * OR_FLAT_TOL;
+        ch = OR_FLAT_TOL * OR_FLAT_TOL;
+        cr = OR_FLAT_TOL;
+        cls = k;
+    } else {
+        s = (Q[4] + Q[7]) + Q[9];
+        cp = OR_FLAT_TOL / 3.0;
+        cv = OR_FLAT_TOL * OR_FLAT_TOL / 3.0;
+        ch = OR_FLAT_TOL * OR_FLAT_TOL / 27.0;
+        cr = OR_FLAT_TOL / 9.0;
+        cls = k == 0 ? 0 : k <= 3 ? 1 : k <= 9 ? 2 : k <= 12 ? 3 : 4;
+    }
+    switch (cls) {
+    case 0: return m <= OR_FLAT_TOL * rho;
+    case 1: return (m * m) * rho <= cv * s;
+    case 2: return m <= cp * s;
+    case 3: return (m * m) * rho <= ((ch * s) * s) * s;
+    default: return m * rho <= (cr * s) * s;
+    }
+}
+
 /* Shared most-stringent limiter (Sec. 3.2).  Reading, per primitive k with
  * dm = Q_i - Q_{i-1}, dp = Q_{i+1} - Q_i, c = (dm + dp)/2:
- *   phi_k = 1 if dm = dp = 0;  0 if dm*dp <= 0;
+ *   phi_k = 1 if the field is flat across the stencil (both differences
+ *           exactly zero, or field_flat: such differences are round-off of
+ *           the conserved-to-primitive recovery -- a field that is uniform
+ *           or zero in exact arithmetic must not limit the others, or the
+ *           scheme drops to first order wherever round-off changes sign);
+ *   phi_k = 0 if dm*dp <= 0;
  *   minmod(dm, dp)/c (minmod) or 2 dm dp/(dm^2 + dp^2) (van Albada) else;
  * phi = min_k phi_k and the slope of every field is phi * c_k. */
 static real shared_phi(const or_cfg *c, const real *Qm, const real *Q0,
@@ -647,8 +691,9 @@ static real shared_phi(const or_cfg *c, const real *Qm, const real *Q0,
     real phi = 1.0;
     for (int k = 0; k < nf; ++k) {
         real dm = Q0[k] - Qm[k], dp = Qp[k] - Q0[k];
+        real m = fabs(dm) > fabs(dp) ? fabs(dm) : fabs(dp);
         real pk;
-        if (dm == 0.0 && dp == 0.0) pk = 1.0;
+        if ((dm == 0.0 && dp == 0.0) || field_flat(c, Q0, k, m)) pk = 1.0;
         else if (dm * dp <= 0.0) pk = 0.0;
         else if (c->limiter == OR_LIM_VANALBADA) pk = 2.0 * dm * dp / (dm * dm + dp * dp);
         else {

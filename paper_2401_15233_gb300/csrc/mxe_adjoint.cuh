@@ -859,12 +859,15 @@ struct PhiAdj {
 };
 
 // Shared limiter from the stencil differences dm = q0 - qm, dp = qp - q0.
+// A flat field (the flat test against the centre cell fr) has phi_k = 1 and
+// never sets phi.
 template <class T, int NF>
-__device__ __forceinline__ PhiAdj<T> phi_adj_d(const T* dm, const T* dp, int lim) {
+__device__ __forceinline__ PhiAdj<T> phi_adj_d(const T* dm, const T* dp, int lim,
+                                               const FlatRef<T>& fr) {
     PhiAdj<T> r{T(1.0), T(0.0), T(0.0), -1};
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const T pk = phi_field(dm[k], dp[k], lim);
+        const T pk = phi_field(dm[k], dp[k], lim, field_flat<NF>(fr, k, abs_max(dm[k], dp[k])));
         if (pk < r.phi) {
             r.phi = pk;
             r.ks = k;
@@ -901,7 +904,7 @@ __device__ __forceinline__ PhiAdj<T> phi_adj(const T* qm, const T* q0, const T* 
         dm[k] = q0[k] - qm[k];
         dp[k] = qp[k] - q0[k];
     }
-    return phi_adj_d<T, NF>(dm, dp, lim);
+    return phi_adj_d<T, NF>(dm, dp, lim, flat_ref<NF>(q0, 1));
 }
 
 // Reverse of the MUSCL face value qf = q0 + hs (phi cen), cen = (dm + dp)/2,

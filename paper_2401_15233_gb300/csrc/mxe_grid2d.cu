@@ -124,10 +124,12 @@ __device__ __forceinline__ void riemann_f64(const double* QL, const double* QR,
 template <int NF>
 __device__ __forceinline__ double phi_box(const double* W, int c, int stride, int lim) {
     double phi = 1.0;
+    const FlatRef<double> fr = flat_ref<NF>(W + c, NBOX);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         const double* w = W + k * NBOX + c;
-        double pk = phi_field(w[0] - w[-stride], w[stride] - w[0], lim);
+        const double dm = w[0] - w[-stride], dp = w[stride] - w[0];
+        double pk = phi_field(dm, dp, lim, field_flat<NF>(fr, k, abs_max(dm, dp)));
         phi = pk < phi ? pk : phi;
     }
     return phi;

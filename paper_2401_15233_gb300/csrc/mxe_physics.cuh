@@ -751,10 +751,89 @@ __device__ __forceinline__ void relax14_prim(T* W, T g, T* N) {
 
 // ---------------------------------------------------------------- limiter
 // Shared most-stringent limiter (Sec. 3.2): phi = min_k phi_k with
-// phi_k = 1 (dm = dp = 0), 0 (dm dp <= 0), min(|dm|,|dp|)/(|dm+dp|/2)
-// (minmod) or 2 dm dp/(dm^2 + dp^2) (van Albada).
+// phi_k = 1 (flat: |dm| and |dp| both within the field's tolerance, or both
+// zero), 0 (dm dp <= 0), min(|dm|,|dp|)/(|dm+dp|/2) (minmod) or
+// 2 dm dp/(dm^2 + dp^2) (van Albada).
+//
+// The flat-field test is a reading (the paper states no tolerance): a
+// field that is uniform or zero in exact arithmetic carries round-off from
+// the conserved-to-primitive recovery, and letting the random signs of
+// those differences zero the shared limiter drops the scheme to first order
+// wherever one field is uniform.  Field k is flat when m = max(|dm|, |dp|)
+// is within T = 1e-10 times its natural scale at the centre cell (theta =
+// p / rho, p the mean pressure): rho; sqrt(theta) (velocities); p (pressure
+// tensor); p sqrt(theta) (heat fluxes); p theta (fourth moment).  The
+// comparisons are multiplied out so that no division or square root enters,
+// with s = P (5-moment) or s = tr P = 3p (14-moment):
+//   m <= T rho;  m^2 rho <= T^2 p;  m <= T p;  m^2 rho <= T^2 p^3;  m rho <= T p^2.
+// The FP32 primitives of the mixed path take the same test and also count
+// a field as flat when m <= 2^-16 |Q_i,k| (128 to 256 FP32 ulps of the
+// centre value): in a uniform non-zero field the FP32 flux differences
+// leave a random walk of a few ulps per sqrt(step) in the FP64 state, which
+// the natural-scale bound alone would let through.
 template <class T>
-__device__ __forceinline__ T phi_field(T dm, T dp, int lim) {
+struct FlatConst;
+template <>
+struct FlatConst<double> {
+    static constexpr double tol = 1e-10;
+};
+template <>
+struct FlatConst<float> {
+    static constexpr float tol = 1e-10f;
+};
+constexpr float FLAT_REL_F32 = 1.52587890625e-5f;     // 2^-16
+
+// scale class of field k in the 5-field, planar 10-field and general
+// 14-field primitive layouts: 0 rho, 1 velocity, 2 pressure tensor,
+// 3 heat flux, 4 fourth moment
+template <int NF>
+__host__ __device__ constexpr int flat_class(int k) {
+    return NF == 5 ? k
+         : NF == 10 ? (k == 0 ? 0 : k <= 2 ? 1 : k <= 6 ? 2 : k <= 8 ? 3 : 4)
+                    : (k == 0 ? 0 : k <= 3 ? 1 : k <= 9 ? 2 : k <= 12 ? 3 : 4);
+}
+
+// density and pressure measure s of the stencil's centre cell
+template <class T>
+struct FlatRef {
+    T rho, s;
+};
+
+// FlatRef of the primitive cell whose field k sits at w[k * fs]
+template <int NF, class T>
+__device__ __forceinline__ FlatRef<T> flat_ref(const T* w, int fs) {
+    T s;
+    if (NF == 5) s = w[2 * fs];
+    else if (NF == 10) s = add_rn(add_rn(w[3 * fs], w[5 * fs]), w[6 * fs]);
+    else s = add_rn(add_rn(w[4 * fs], w[7 * fs]), w[9 * fs]);
+    return FlatRef<T>{w[0], s};
+}
+
+// the flat test of field k (compile-time index) with m = max(|dm|, |dp|)
+template <int NF, class T>
+__device__ __forceinline__ bool field_flat(const FlatRef<T>& f, int k, T m) {
+    constexpr T t = FlatConst<T>::tol;
+    constexpr T cp = NF == 5 ? t : t / T(3);
+    constexpr T cv = NF == 5 ? t * t : t * t / T(3);
+    constexpr T ch = NF == 5 ? t * t : t * t / T(27);
+    constexpr T cr = NF == 5 ? t : t / T(9);
+    switch (flat_class<NF>(k)) {
+    case 0: return m <= mul_rn(t, f.rho);
+    case 1: return mul_rn(mul_rn(m, m), f.rho) <= mul_rn(cv, f.s);
+    case 2: return m <= mul_rn(cp, f.s);
+    case 3: return mul_rn(mul_rn(m, m), f.rho) <= mul_rn(mul_rn(mul_rn(ch, f.s), f.s), f.s);
+    default: return mul_rn(m, f.rho) <= mul_rn(mul_rn(cr, f.s), f.s);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T abs_max(T a, T b) {
+    return fmax(fabs(a), fabs(b));
+}
+
+template <class T>
+__device__ __forceinline__ T phi_field(T dm, T dp, int lim, bool flat) {
+    if (flat) return T(1);
     if (mul_rn(dm, dp) > T(0)) {
         if (lim == 1)
             return mul_rn(mul_rn(T(2), dm), dp) / add_rn(mul_rn(dm, dm), mul_rn(dp, dp));

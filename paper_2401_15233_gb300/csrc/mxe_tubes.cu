@@ -148,10 +148,13 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
             double phi = 0.0;
             if (a.sp.order == 2) {
                 phi = 1.0;
+                const FlatRef<double> fr = flat_ref<NF>(W + c, BOX1);
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
                     const double* w = W + k * BOX1 + c;
-                    double pk = phi_field(w[0] - w[-1], w[1] - w[0], a.sp.limiter);
+                    const double dm = w[0] - w[-1], dp = w[1] - w[0];
+                    double pk = phi_field(dm, dp, a.sp.limiter,
+                                          field_flat<NF>(fr, k, abs_max(dm, dp)));
                     phi = pk < phi ? pk : phi;
                 }
             }

@@ -102,17 +102,21 @@ __device__ __forceinline__ void load_w(const TubeMixedArgs& a, const float* Wt, 
 template <int NF, int BOX>
 __device__ __forceinline__ float phi_1d(const float* W, int c, int lim) {
     float phi = 1.0f;
+    const FlatRef<float> fr = flat_ref<NF>(W + c, BOX);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         const float* w = W + k * BOX + c;
         float dm = w[0] - w[-1], dp = w[1] - w[0];
+        const float m = abs_max(dm, dp);
         float pk;
-        if (dm * dp > 0.0f) {
-            if (lim == 1) {
-                pk = 2.0f * dm * dp / (dm * dm + dp * dp);
+        if (m <= FLAT_REL_F32 * fabsf(w[0]) || field_flat<NF>(fr, k, m)) {
+            pk = 1.0f;
+        } else if (dm * dp > 0.0f) {
+            if (lim == 1) {      // approximate quotient (2 ulp): the limiter is a ratio
+                pk = __fdividef(2.0f * dm * dp, dm * dm + dp * dp);
             } else {
                 float am = fabsf(dm), ap = fabsf(dp);
-                pk = 2.0f * fminf(am, ap) / (am + ap);
+                pk = __fdividef(2.0f * fminf(am, ap), am + ap);
             }
         } else {
             pk = (dm == 0.0f && dp == 0.0f) ? 1.0f : 0.0f;
