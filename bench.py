@@ -44,12 +44,12 @@ BYTES_PER_CELL_UPDATE = {("fp64", False): 560.0, ("mixed", False): 504.0,
 # DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the two stage launches of one step, 2048^2
 # crossed jets, 4.19e6 cells; scaled to the benchmark grid by cell count)
-TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 341.2}
+TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 340.5}
 # Issue-rate roofline of the mixed planar stage kernel (it is bound by
 # instruction issue, not by DRAM): thread instructions per cell-update over
 # both stages (ncu smsp__inst_executed.sum x 32 / cells, 1024^2 crossed
 # jets) against 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
-THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 6734.0}
+THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 7094.5}
 KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed",
           ("fp64", True): "mxe_stage14_2d_f64_planar", ("mixed", True): "mxe_stage14_2d_mixed_planar_b3"}
 

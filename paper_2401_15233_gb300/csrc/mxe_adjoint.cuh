@@ -867,8 +867,8 @@ __device__ __forceinline__ PhiAdj<T> phi_adj_d(const T* dm, const T* dp, int lim
     PhiAdj<T> r{T(1.0), T(0.0), T(0.0), -1};
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const T pk = phi_field(dm[k], dp[k], lim, field_flat<NF>(fr, k, abs_max(dm[k], dp[k])));
-        if (pk < r.phi) {
+        const T pk = phi_field(dm[k], dp[k], lim);
+        if (pk < r.phi && !field_flat<NF>(fr, k, abs_max(dm[k], dp[k]))) {
             r.phi = pk;
             r.ks = k;
             if (mul_rn(dm[k], dp[k]) > T(0.0)) {

@@ -128,9 +128,7 @@ __device__ __forceinline__ double phi_box(const double* W, int c, int stride, in
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         const double* w = W + k * NBOX + c;
-        const double dm = w[0] - w[-stride], dp = w[stride] - w[0];
-        double pk = phi_field(dm, dp, lim, field_flat<NF>(fr, k, abs_max(dm, dp)));
-        phi = pk < phi ? pk : phi;
+        phi_accumulate<NF>(phi, w[0] - w[-stride], w[stride] - w[0], lim, fr, k);
     }
     return phi;
 }

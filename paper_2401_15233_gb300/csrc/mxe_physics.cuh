@@ -831,9 +831,9 @@ __device__ __forceinline__ T abs_max(T a, T b) {
     return fmax(fabs(a), fabs(b));
 }
 
+// phi_k without the flat-field test (1 only when dm = dp = 0)
 template <class T>
-__device__ __forceinline__ T phi_field(T dm, T dp, int lim, bool flat) {
-    if (flat) return T(1);
+__device__ __forceinline__ T phi_field(T dm, T dp, int lim) {
     if (mul_rn(dm, dp) > T(0)) {
         if (lim == 1)
             return mul_rn(mul_rn(T(2), dm), dp) / add_rn(mul_rn(dm, dm), mul_rn(dp, dp));
@@ -842,6 +842,17 @@ __device__ __forceinline__ T phi_field(T dm, T dp, int lim, bool flat) {
         return mn / mul_rn(T(0.5), add_rn(am, ap));
     }
     return (dm == T(0) && dp == T(0)) ? T(1) : T(0);
+}
+
+// phi = min(phi, phi_k) for field k (compile-time index) of the stencil
+// centred on the cell fr.  A flat field has phi_k = 1, which never lowers
+// phi, so the flat test runs only where phi_k without it would: the result
+// is the min over all fields either way.
+template <int NF, class T>
+__device__ __forceinline__ void phi_accumulate(T& phi, T dm, T dp, int lim, const FlatRef<T>& fr,
+                                               int k) {
+    const T pk = phi_field(dm, dp, lim);
+    if (pk < phi && !field_flat<NF>(fr, k, abs_max(dm, dp))) phi = pk;
 }
 
 // MUSCL face value Q0 + sgn/2 (phi c) with the central difference

@@ -152,10 +152,7 @@ __device__ double tube_stage(const TubeArgs& a, const TubeDesc& td, const double
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
                     const double* w = W + k * BOX1 + c;
-                    const double dm = w[0] - w[-1], dp = w[1] - w[0];
-                    double pk = phi_field(dm, dp, a.sp.limiter,
-                                          field_flat<NF>(fr, k, abs_max(dm, dp)));
-                    phi = pk < phi ? pk : phi;
+                    phi_accumulate<NF>(phi, w[0] - w[-1], w[1] - w[0], a.sp.limiter, fr, k);
                 }
             }
             ph[idx] = phi;

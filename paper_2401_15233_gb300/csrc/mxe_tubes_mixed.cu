@@ -107,11 +107,8 @@ __device__ __forceinline__ float phi_1d(const float* W, int c, int lim) {
     for (int k = 0; k < NF; ++k) {
         const float* w = W + k * BOX + c;
         float dm = w[0] - w[-1], dp = w[1] - w[0];
-        const float m = abs_max(dm, dp);
         float pk;
-        if (m <= FLAT_REL_F32 * fabsf(w[0]) || field_flat<NF>(fr, k, m)) {
-            pk = 1.0f;
-        } else if (dm * dp > 0.0f) {
+        if (dm * dp > 0.0f) {
             if (lim == 1) {      // approximate quotient (2 ulp): the limiter is a ratio
                 pk = __fdividef(2.0f * dm * dp, dm * dm + dp * dp);
             } else {
@@ -121,7 +118,10 @@ __device__ __forceinline__ float phi_1d(const float* W, int c, int lim) {
         } else {
             pk = (dm == 0.0f && dp == 0.0f) ? 1.0f : 0.0f;
         }
-        phi = fminf(pk, phi);
+        if (pk < phi) {          // a flat field (phi_k = 1) never lowers phi
+            const float m = abs_max(dm, dp);
+            if (!(m <= FLAT_REL_F32 * fabsf(w[0]) || field_flat<NF>(fr, k, m))) phi = pk;
+        }
     }
     return phi;
 }
