@@ -73,9 +73,10 @@ def free_run_drift(mx, s, orc, cfg, U, nsteps, t_end):
     """Both sides march on their own CFL clocks from the same state, one step
     at a time; returns (first step whose state differs by more than 1e-12,
     final per-field drift, final times).  The shared most-stringent limiter
-    makes the scheme branch on the sign of noise-level differences, so
-    free trajectories separate after a while; that is reported, the per-step
-    parity above is the gate."""
+    branches on the sign of small differences (the non-equilibrium tails
+    ahead of the Sod waves cross zero), so rounding differences of the
+    closure can flip it and free trajectories separate after a while; that is
+    reported, the per-step parity above is the gate."""
     s.set_state(aos_to_soa(U), kind="conserved")
     first = None
     t = 0.0
