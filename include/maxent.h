@@ -6,7 +6,11 @@
  * Torrilhon, as used by Boccelli, Kaufmann, Magin & McDonald (JCP 2024,
  * arXiv 2401.15233), with an explicit cell-centred finite-volume scheme:
  * MUSCL reconstruction of primitive moments with one shared limiter
- * (Sec. 3.2), HLL or Rusanov face fluxes (Sec. 3.1) with the approximate
+ * (Sec. 3.2; a field whose two stencil differences are both within 1e-10
+ * of its natural scale -- rho, sqrt(p/rho), p, p sqrt(p/rho), p^2/rho --
+ * counts as flat and does not limit the others, so round-off in a field
+ * that is uniform in exact arithmetic cannot drop the scheme to first
+ * order), HLL or Rusanov face fluxes (Sec. 3.1) with the approximate
  * wave speeds of Sec. 5 / Appendix B, BGK relaxation sources (Sec. 2.3,
  * 2.4), forward Euler or midpoint RK2 in time (Sec. 3) under a CFL condition.
  *
@@ -303,8 +307,9 @@ mxe_status mxe_set_adjoint_precision(mxe_ctx *ctx, int precision);
  * the limiter value phi is held constant in the derivative, a common choice
  * for adjoints of limited schemes: the shared most-stringent limiter is not
  * differentiable at the scale of finite differences where a field's
- * differences are near round-off, and its derivative there scales as the
- * inverse of those differences.  MXE_EINVAL for another value. */
+ * differences are small, and its derivative there scales as the inverse of
+ * those differences (differences at round-off level count as flat and do
+ * not select phi in either mode).  MXE_EINVAL for another value. */
 mxe_status mxe_set_adjoint_limiter(mxe_ctx *ctx, int frozen);
 
 /* Adjoint of the residual L(U) = -div F + C at the conserved state U
