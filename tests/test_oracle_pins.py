@@ -423,3 +423,148 @@ def test_ws14_transverse_heat_flux_terms(orc):
     z = 0.3 + 0.5 * (0.6 * 4 - 0.76 + 0.35)
     want2 = 0.5 * (a2 + b2) * (z + math.sqrt(z * z + 4 + 0.025))
     assert orc.lambda_star14(2.0, 0.3, 0.5, 1.0) == pytest.approx(want2, rel=1e-14)
+
+
+# ------------------------------------------- a7: 5-moment fit away from q* = 0
+def test_baradaran_worked_values_off_axis(orc):
+    """Eq. (ws-max-baradaran-orig) at sigma = 1e-4, q* = +-1/2, against the
+    hand evaluation in tests/golden/ws5_worked.txt.  The q* < 0 value comes
+    from the rationalised bracket (reading: no cancellation) and also pins
+    lambda*_min(q*) = -lambda*_max(-q*) through the re-dimensionalised
+    speeds of a state with that q*."""
+    g = read_golden("ws5_worked.txt")
+    assert orc.lambda_star5(0.5, 1e-4) == pytest.approx(float(g["lam_max_q+05_s1e-4"]), rel=1e-13)
+    assert orc.lambda_star5(-0.5, 1e-4) == pytest.approx(float(g["lam_max_q-05_s1e-4"]), rel=1e-13)
+    # a state with rho = 2, u = 0.3, P = 8 (theta = 4), q* = 1/2 and the sigma
+    # of r* chosen so that sigma = 1e-4 exactly in real arithmetic:
+    # r* = 3 - 2 sigma + q*^2/sigma (Eq. sigma-mapping-5mom inverted)
+    rho, u, th, qs, sg = 2.0, 0.3, 4.0, 0.5, 1e-4
+    rs = 3 - 2 * sg + qs * qs / sg
+    Q = [rho, u, rho * th, qs * rho * th ** 1.5, rs * rho * th * th]
+    lo, hi = orc.wavespeeds(Q, 1e-6, 1.0)
+    assert hi == pytest.approx(u + 2.0 * float(g["lam_max_q+05_s1e-4"]), rel=1e-9)
+    assert lo == pytest.approx(u - 2.0 * float(g["lam_max_q-05_s1e-4"]), rel=1e-9)
+
+
+def test_baradaran_on_realizability_boundary_is_two_delta_speed(orc):
+    """At sigma = 1 the distribution is two delta functions (Sec. 2.3.1).
+    With zero mean and unit variance their velocities c1 < 0 < c2 satisfy
+    c1 c2 = -1 and c1 + c2 = q* (the third moment), so the fastest and
+    slowest signals travel at (q* +- sqrt(q*^2 + 4))/2.  Eq.
+    (ws-max-baradaran-orig) must return exactly these: C = E = 0 there, so
+    this fixes the hyperbolic part (its 1/(2 sigma) factor, the sign of q*
+    and the 4 sigma^2 Y term with Y = 1)."""
+    for qs in (-3.0, -0.5, 0.0, 0.25, 2.0):
+        r = math.sqrt(qs * qs + 4)
+        assert orc.lambda_star5(qs, 1.0) == pytest.approx((qs + r) / 2, rel=1e-14)
+        assert -orc.lambda_star5(-qs, 1.0) == pytest.approx((qs - r) / 2, rel=1e-14)
+    # the same from a two-particle cloud, through the full speed routine
+    for (w1, w2, v1, v2) in [(0.3, 0.7, -1.1, 2.4), (0.8, 0.2, 0.5, 3.0)]:
+        m = wl.particle_moments5(np.array([w1, w2]), np.array([v1, v2]))
+        lo, hi = orc.wavespeeds(m, 1e-4, 1.0)
+        assert orc.sigma(m) == pytest.approx(1.0, abs=1e-12)
+        assert hi == pytest.approx(v2, rel=1e-6)
+        assert lo == pytest.approx(v1, rel=1e-6, abs=1e-6)
+
+
+def test_baradaran_small_sigma_asymptotes(orc):
+    """Closed-form limits of Eq. (ws-max-baradaran-orig) as sigma -> 0 at
+    fixed q* != 0 (C -> sqrt 3, E -> 0.8 sqrt 3):
+      q* > 0: the bracket is 2q* + D0/(2q*) + O(sigma^2), so
+              lambda* - q*/sigma -> E - C/5 = (3/5) sqrt 3;
+      q* < 0: the bracket is D0/(2|q*|) + O(sigma^2), so
+              lambda* -> E + C/5 = sqrt 3.
+    A dropped or sign-flipped (4/5) q* sigma C term moves the first limit to
+    0.8 sqrt 3 or sqrt 3 and the second to 0.8 sqrt 3 or (3/5) sqrt 3.  At
+    sigma = 1e-14 the unrationalised bracket for q* < 0 loses ~1e-3 to
+    cancellation, so the second limit also pins the rationalised form."""
+    r3 = math.sqrt(3.0)
+    for qs in (0.5, 2.0):
+        s = 1e-6
+        assert orc.lambda_star5(qs, s) - qs / s == pytest.approx(0.6 * r3, rel=1e-4)
+    for qs in (-0.5, -2.0):
+        assert orc.lambda_star5(qs, 1e-14) == pytest.approx(r3, rel=1e-9)
+
+
+# ----------------------------------------------------------- a9: tau model
+@pytest.mark.parametrize("system", [5, 14])
+def test_tau_follows_mean_free_path_over_thermal_speed(orc, system):
+    """Sec. 4: tau = (n sigma_cs v_th)^-1 with v_th = sqrt(8 k_B T / (pi m));
+    Kn = lambda_ref / L with lambda_ref = 1/(n_ref sigma_cs) (the jets'
+    sqrt(2) in lambda cancels the same way, Sec. 6).  Units: m = k_B = 1,
+    n = rho; T = P/rho (1D1V) or tr P/(3 rho) (3D3V).  The cross-section is
+    recovered from Kn and tau evaluated from its definition at two states
+    that differ from the reference in both rho and T (an anisotropic P for
+    14 moments), against the oracle's tau_ref (rho_ref/rho) sqrt(T_ref/T)."""
+    Kn, L, rho_ref, T_ref = 0.03, 0.1, 1.0, 1.5
+    sig_cs = 1.0 / (Kn * L * rho_ref)
+    vth = lambda T: math.sqrt(8.0 * T / math.pi)
+    tau_def = lambda rho, T: 1.0 / (rho * sig_cs * vth(T))
+    cfg = orc.make_cfg(system=system, nx=4, tau_model=orc.TAU_HARDSPHERE,
+                       tau_ref=tau_def(rho_ref, T_ref), rho_ref=rho_ref, T_ref=T_ref)
+    for rho, T in [(0.125, 0.8), (2.0, 3.0)]:
+        if system == 5:
+            Q = [rho, 0.7, rho * T, 0.1 * rho * T ** 1.5, 3.2 * rho * T * T]
+        else:
+            Q = list(wl.maxwellian14(rho, 0.4, -0.2, T))
+            Q[4] += 0.3 * rho * T; Q[7] -= 0.1 * rho * T; Q[9] -= 0.2 * rho * T   # tr P kept
+            Q[5] += 0.05 * rho * T
+        assert orc.tau(cfg, np.array(Q, dtype=float)) == pytest.approx(tau_def(rho, T), rel=1e-14)
+    # hand value: Kn = 0.01, L = 1, rho_ref = T_ref = 1 at rho = 0.125, T = 0.8:
+    # tau = 0.01 / (0.125 * 1.42729929) = 0.0560499122
+    cfg1 = orc.make_cfg(system=5, nx=4, tau_model=orc.TAU_HARDSPHERE,
+                        tau_ref=wl.sod_tau_ref(0.01), rho_ref=1.0, T_ref=1.0)
+    assert orc.tau(cfg1, np.array([0.125, 0.0, 0.1, 0.0, 0.24])) == pytest.approx(0.0560499122, rel=1e-9)
+
+
+# ------------------------------------------------------- a11: CFL rate and dt
+LAM14_ISO = 2.1825987   # lambda* of a Maxwellian (sigma clamped to 1e-4), ws14_worked.txt
+LAM5_ISO = 2.8455181    # Baradaran at q* = 0, sigma = 1e-4 (design-survey hand evaluation)
+
+
+def test_cfl_rate_and_dt_2d_by_hand(orc):
+    """Reading 10: dt = CFL / max_cells sum_d max(|lmin_d|, |lmax_d|)/dx_d.
+    Maxwellian cells (q = 0, sigma clamped to sigma_lim) have
+    lmax/lmin = u_d +- lambda* sqrt(T), so each cell's rate is
+    (|u_x| + lambda* sqrt T)/dx + (|u_y| + lambda* sqrt T)/dy.  The states
+    are chosen so that the cell with the largest sum (B) differs from the
+    cell with the largest single-direction term (A), and dx != dy; the last
+    step is clipped to t_end."""
+    g = read_golden("ws14_worked.txt")
+    lam = float(g["lam_q0_s1e-4"])
+    assert lam == LAM14_ISO
+    nx, ny, dx, dy = 3, 2, 1.0 / 3.0, 1.0 / 2.0
+    cells = {(0, 0): (1.0, 6.0, 0.0, 1.0),      # A: 3*8.18 + 2*2.18 = 28.9
+             (1, 0): (0.5, 4.0, -6.0, 1.0),     # B: 3*6.18 + 2*8.18 = 34.9
+             (2, 0): (1e-3, 0.0, 0.0, 4.0),
+             (0, 1): (1.0, 0.0, 0.0, 1.0),
+             (1, 1): (2.0, -1.0, 1.0, 0.25),
+             (2, 1): (1.0, 0.5, 2.5, 1.0)}
+    prim = np.zeros((ny, nx, 14))
+    want = 0.0
+    for (i, j), (rho, ux, uy, T) in cells.items():
+        prim[j, i] = wl.maxwellian14(rho, ux, uy, T)
+        r = (abs(ux) + lam * math.sqrt(T)) / dx + (abs(uy) + lam * math.sqrt(T)) / dy
+        want = max(want, r)
+    assert want == pytest.approx(3 * (4 + lam) + 2 * (6 + lam))   # cell B
+    cfg = orc.make_cfg(system=14, nx=nx, ny=ny, cfl=0.5)
+    U = orc.prim2cons_field(prim)
+    assert orc.max_rate(cfg, U) == pytest.approx(want, rel=2e-7)
+    dt_full = 0.5 / want
+    assert orc.dt(cfg, U, 0.0, 10.0) == pytest.approx(dt_full, rel=2e-7)
+    assert orc.dt(cfg, U, 1.0, 1.0 + 0.25 * dt_full) == pytest.approx(0.25 * dt_full, rel=1e-9)
+
+
+def test_cfl_rate_and_dt_1d_by_hand(orc):
+    """The same for the 5-moment tube: rate = (|u| + lambda* sqrt T)/dx with
+    Baradaran's lambda*(q* = 0, sigma_lim = 1e-4)."""
+    nx, dx = 4, 0.25
+    cells = [(1.0, -3.0, 1.0), (0.2, 1.0, 4.0), (1.0, 0.0, 1.0), (0.125, 0.5, 0.8)]
+    prim = np.array([wl.maxwellian5(*c) for c in cells])[None]
+    want = max((abs(u) + LAM5_ISO * math.sqrt(T)) / dx for (_, u, T) in cells)
+    assert want == pytest.approx(4 * (1 + 2 * LAM5_ISO))
+    cfg = orc.make_cfg(system=5, nx=nx, ny=1, cfl=0.5)
+    U = orc.prim2cons_field(prim)
+    assert orc.max_rate(cfg, U) == pytest.approx(want, rel=2e-7)
+    assert orc.dt(cfg, U, 0.0, 10.0) == pytest.approx(0.5 / want, rel=2e-7)
+    assert orc.dt(cfg, U, 0.1, 0.1 + 1e-5) == pytest.approx(1e-5, rel=1e-9)
