@@ -346,7 +346,12 @@ mxe_status mxe_adjoint_residual(mxe_ctx *ctx, const double *U, const double *V, 
  *    be serialised by the caller.
  *  - t_out / steps_out (host, may be NULL) receive the final time and the
  *    steps taken; passing either synchronises `stream` (a cudaStream_t, NULL
- *    for the default stream).
+ *    for the default stream).  A non-finite state (MXE_ENONFINITE) is
+ *    detected from the clock read back for them, so it is reported only
+ *    when t_out or steps_out is given; with both NULL the call returns
+ *    MXE_OK once the work is queued.
+ *  - U must hold nf*nx doubles on the current device; the library cannot
+ *    check a raw pointer's extent (the Python binding checks it).
  * Returns MXE_EINVAL for nx > 16384 or any other invalid argument, before
  * any device work. */
 mxe_status mxe_tube_run_noalloc(const mxe_config *cfg, int bc_lo, int bc_hi, int tau_model,

@@ -140,15 +140,45 @@ def _check(ctx, st):
         raise MaxentError(st, msg)
 
 
-def _ptr(a, nbytes=None):
-    """(pointer, on_device) of a numpy array or a CUDA tensor (float64, contiguous)."""
+# Elements per field of every live context (cells of a grid, or of all tubes
+# of a batch), so that every wrapper can check the size of the arrays it
+# hands to the library: the library trusts its pointers.
+_CELLS = {}
+_NF = {}
+
+
+def _ctx_key(ctx):
+    return ctx.value if hasattr(ctx, "value") else int(ctx)
+
+
+def _ptr(a, nelem=None):
+    """(pointer, on_device) of a numpy array or a CUDA tensor (float64,
+    contiguous).  nelem: required number of elements.  A CUDA tensor must
+    live on the current device, where the library launches its kernels."""
     if hasattr(a, "data_ptr"):
         if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
             raise ValueError("tensors must be contiguous float64")
+        if a.is_cuda:
+            import torch
+            if a.device.index != torch.cuda.current_device():
+                raise ValueError(f"tensor on {a.device}, but the current device is "
+                                 f"cuda:{torch.cuda.current_device()}")
+        if nelem is not None and a.numel() != nelem:
+            raise ValueError(f"tensor holds {a.numel()} elements, {nelem} expected")
         return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError("arrays must be C-contiguous float64")
+    if nelem is not None and a.size != nelem:
+        raise ValueError(f"array holds {a.size} elements, {nelem} expected")
     return C.c_void_p(a.ctypes.data), 0
+
+
+def _state_elems(ctx, kind=None):
+    """Elements of a state array of this context (one field for SIGMA)."""
+    k = _ctx_key(ctx)
+    if k not in _CELLS:
+        raise ValueError("unknown or destroyed context")
+    return _CELLS[k] * (1 if kind == SIGMA else _NF[k])
 
 
 # ------------------------------------------------------------ C-named wrappers
@@ -157,10 +187,14 @@ def mxe_create(cfg: Config):
     st = lib().mxe_create(C.byref(cfg), C.byref(h))
     if st != OK:
         raise MaxentError(st, "mxe_create rejected the configuration")
+    _CELLS[_ctx_key(h)] = int(cfg.nx) * int(cfg.ny)
+    _NF[_ctx_key(h)] = int(cfg.system)
     return h
 
 
 def mxe_destroy(ctx):
+    _CELLS.pop(_ctx_key(ctx), None)
+    _NF.pop(_ctx_key(ctx), None)
     lib().mxe_destroy(ctx)
 
 
@@ -173,12 +207,12 @@ def mxe_get_stream(ctx):
 
 
 def mxe_set_state(ctx, kind, arr):
-    p, dev = _ptr(arr)
+    p, dev = _ptr(arr, _state_elems(ctx, kind))
     _check(ctx, lib().mxe_set_state(ctx, kind, p, dev))
 
 
 def mxe_get_moments(ctx, kind, out):
-    p, dev = _ptr(out)
+    p, dev = _ptr(out, _state_elems(ctx, kind))
     _check(ctx, lib().mxe_get_moments(ctx, kind, p, dev))
     return out
 
@@ -240,8 +274,9 @@ def mxe_tube_run_noalloc(cfg: Config, U_dev, t0, t_end, max_steps, bc_lo=BC_TRAN
                          bc_hi=BC_TRANSMISSIVE, tau_model=TAU_NONE, tau_ref=1.0, rho_ref=1.0,
                          T_ref=1.0, stream=None):
     """1D solve on a caller-owned device array (torch CUDA float64 tensor,
-    conserved SoA (nf, nx)) using only the library's fixed device arrays."""
-    p, dev = _ptr(U_dev)
+    conserved SoA (nf, nx)) using only the library's fixed device arrays.
+    U must hold exactly nf*nx elements and live on the current device."""
+    p, dev = _ptr(U_dev, int(cfg.system) * int(cfg.nx))
     if not dev:
         raise ValueError("U must be a device tensor")
     t = C.c_double()
@@ -262,6 +297,8 @@ def mxe_batch_create(cfg: Config, ncells, lengths):
                                 C.byref(h))
     if st != OK:
         raise MaxentError(st, "mxe_batch_create rejected the configuration")
+    _CELLS[_ctx_key(h)] = int(nc.sum())
+    _NF[_ctx_key(h)] = int(cfg.system)
     return h
 
 
@@ -307,7 +344,7 @@ def mxe_adjoint_run(ctx, ubar):
     """ubar: adjoint of the final state (numpy or CUDA tensor, (14, ny, nx)),
     overwritten with the adjoint of the first recorded state.  Returns
     (gbar [4, GHOST_SLOTS, 14], taubar)."""
-    p, dev = _ptr(ubar)
+    p, dev = _ptr(ubar, _state_elems(ctx))
     gb = np.zeros((4, GHOST_SLOTS, 14))
     tb = C.c_double(0.0)
     _check(ctx, lib().mxe_adjoint_run(ctx, p, dev, C.c_void_p(gb.ctypes.data), C.byref(tb)))
@@ -315,9 +352,10 @@ def mxe_adjoint_run(ctx, ubar):
 
 
 def mxe_adjoint_residual(ctx, U, V, out):
-    pu, du = _ptr(U)
-    pv, dv = _ptr(V)
-    po, do = _ptr(out)
+    n = _state_elems(ctx)
+    pu, du = _ptr(U, n)
+    pv, dv = _ptr(V, n)
+    po, do = _ptr(out, n)
     if not (du == dv == do):
         raise ValueError("U, V and out must all be on the host or all on the device")
     gb = np.zeros((4, GHOST_SLOTS, 14))

@@ -62,6 +62,16 @@ static cudaError_t noalloc_ptrs(NoallocPtrs& out) {
     return cudaSuccess;
 }
 
+// Writes the tube descriptor and a fresh clock into the fixed arrays.  Both
+// arrive by value as kernel arguments, so no host buffer has to outlive the
+// call (a cudaMemcpyAsync from a stack variable would).
+__global__ void mxe_noalloc_init(const TubeDesc td, const TubeClock ck) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        g_tube[0] = td;
+        g_clock[0] = ck;
+    }
+}
+
 }  // namespace mxe
 
 using namespace mxe;
@@ -101,9 +111,8 @@ extern "C" mxe_status mxe_tube_run_noalloc(const mxe_config* cfg, int bc_lo, int
     td.rp = RelaxParams{tau_model, tau_ref, rho_ref, T_ref};
     TubeClock ck{};               // the clock must start from t0 with no steps and no status
     ck.t = t0;
-    if (cudaMemcpyAsync(p.tube, &td, sizeof td, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(p.clock, &ck, sizeof ck, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return MXE_ECUDA;
+    mxe_noalloc_init<<<1, 32, 0, st>>>(td, ck);
+    if (cudaGetLastError() != cudaSuccess) return MXE_ECUDA;
 
     TubeArgs a{};
     a.U = U;

@@ -71,3 +71,18 @@ def test_invalid_batches_rejected_without_gpu():
         with pytest.raises(mx.MaxentError) as e:
             mx.Batch(ncells, lengths, **({"system": 14} | kw))
         assert e.value.status == mx.EINVAL, (ncells, lengths, kw)
+
+
+def test_binding_checks_array_size_before_passing_a_pointer():
+    """The library trusts its pointers; the binding refuses an array whose
+    element count differs from what the call will read or write."""
+    import numpy as np
+    import paper_2401_15233_gb300 as mx
+    p, dev = mx._ptr(np.zeros(6), 6)
+    assert dev == 0 and p.value is not None
+    with pytest.raises(ValueError):
+        mx._ptr(np.zeros(5), 6)
+    with pytest.raises(ValueError):
+        mx._ptr(np.zeros(6, dtype=np.float32), 6)
+    with pytest.raises(ValueError):
+        mx._state_elems(mx._P(12345))      # not a live context
