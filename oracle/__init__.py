@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "maxent_oracle.c")
 _LIB = os.path.join(_HERE, "libmaxent_oracle.so")
+_OMPLIB = os.path.join(_HERE, "libmaxent_oracle_omp.so")
 _TSRC = os.path.join(_HERE, "tangent.cpp")
 _TLIB = os.path.join(_HERE, "libmaxent_oracle_tangent.so")
 
@@ -29,16 +30,21 @@ MAX_SPANS = 4
 MARGIN = 4
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction).  omp=True: the
+    OpenMP timing build (same arithmetic, loops over rows and columns on
+    all host cores; bitwise equal results)."""
+    out = _OMPLIB if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "maxent_oracle.h"))
     ):
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-fPIC", "-shared", "-o", out + ".tmp", _SRC, "-lm"]
+        if omp:
+            cmd.insert(1, "-fopenmp")
         subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(out + ".tmp", out)
+    return out
 
 
 def build_tangent(force: bool = False) -> str:
@@ -87,50 +93,72 @@ _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
-        for name in ("or5_prim2cons", "or5_cons2prim", "or14_prim2cons", "or14_cons2prim"):
-            getattr(L, name).argtypes = [_dp, _dp]
-            getattr(L, name).restype = None
-        L.or5_sigma.argtypes = [_dp]; L.or5_sigma.restype = C.c_double
-        L.or14_sigma.argtypes = [_dp]; L.or14_sigma.restype = C.c_double
-        L.or5_closure.argtypes = [_dp, C.c_double]; L.or5_closure.restype = C.c_double
-        L.or5_flux_given_s.argtypes = [_dp, C.c_double, _dp]; L.or5_flux_given_s.restype = None
-        L.or5_flux.argtypes = [_dp, C.c_double, _dp]; L.or5_flux.restype = None
-        L.or5_lambda_star_max.argtypes = [C.c_double, C.c_double]
-        L.or5_lambda_star_max.restype = C.c_double
-        L.or5_wavespeeds.argtypes = [_dp, C.c_double, C.c_double,
-                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
-        L.or5_wavespeeds.restype = None
-        L.or5_source.argtypes = [_dp, C.c_double, _dp]; L.or5_source.restype = None
-        L.or14_closure.argtypes = [_dp, C.c_double, _dp, _dp, _dp]
-        L.or14_closure.restype = None
-        L.or14_flux_given_closure.argtypes = [_dp, _dp, _dp, _dp, C.c_int, _dp]
-        L.or14_flux_given_closure.restype = None
-        L.or14_flux.argtypes = [_dp, C.c_double, C.c_int, _dp]; L.or14_flux.restype = None
-        L.or14_lambda_star_max.argtypes = [C.c_double] * 4
-        L.or14_lambda_star_max.restype = C.c_double
-        L.or14_wavespeeds.argtypes = [_dp, C.c_int, C.c_double, C.c_double,
-                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
-        L.or14_wavespeeds.restype = None
-        L.or14_source.argtypes = [_dp, C.c_double, _dp]; L.or14_source.restype = None
-        L.or_block_step.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
-                                    _dp, C.c_double, _dp]
-        L.or_block_step.restype = C.c_int
-        L.or_block_residual.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
-                                        _dp, _dp]
-        L.or_block_residual.restype = C.c_int
-        L.or_max_rate.argtypes = [C.POINTER(Cfg), _dp]; L.or_max_rate.restype = C.c_double
-        L.or_dt.argtypes = [C.POINTER(Cfg), _dp, C.c_double, C.c_double]
-        L.or_dt.restype = C.c_double
-        L.or_step.argtypes = [C.POINTER(Cfg), _dp, C.c_double]; L.or_step.restype = C.c_int
-        L.or_run.argtypes = [C.POINTER(Cfg), _dp, C.POINTER(C.c_double), C.c_double,
-                             C.c_int, C.c_void_p]
-        L.or_run.restype = C.c_int
-        L.or_tau.argtypes = [C.POINTER(Cfg), _dp]; L.or_tau.restype = C.c_double
-        L.or_prim2cons_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_prim2cons_n.restype = None
-        L.or_cons2prim_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_cons2prim_n.restype = None
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+_omplib = None
+
+
+def lib_omp():
+    """The OpenMP timing build (thread count from OMP_NUM_THREADS, else all
+    cores).  Same functions as lib()."""
+    global _omplib
+    if _omplib is None:
+        _omplib = _declare(C.CDLL(build(omp=True)))
+    return _omplib
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the scheme loops of that build use."""
+    return (lib_omp() if omp else lib()).or_threads()
+
+
+def _declare(L):
+    """argument and result types of the exported functions"""
+    for name in ("or5_prim2cons", "or5_cons2prim", "or14_prim2cons", "or14_cons2prim"):
+        getattr(L, name).argtypes = [_dp, _dp]
+        getattr(L, name).restype = None
+    L.or5_sigma.argtypes = [_dp]; L.or5_sigma.restype = C.c_double
+    L.or14_sigma.argtypes = [_dp]; L.or14_sigma.restype = C.c_double
+    L.or5_closure.argtypes = [_dp, C.c_double]; L.or5_closure.restype = C.c_double
+    L.or5_flux_given_s.argtypes = [_dp, C.c_double, _dp]; L.or5_flux_given_s.restype = None
+    L.or5_flux.argtypes = [_dp, C.c_double, _dp]; L.or5_flux.restype = None
+    L.or5_lambda_star_max.argtypes = [C.c_double, C.c_double]
+    L.or5_lambda_star_max.restype = C.c_double
+    L.or5_wavespeeds.argtypes = [_dp, C.c_double, C.c_double,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.or5_wavespeeds.restype = None
+    L.or5_source.argtypes = [_dp, C.c_double, _dp]; L.or5_source.restype = None
+    L.or14_closure.argtypes = [_dp, C.c_double, _dp, _dp, _dp]
+    L.or14_closure.restype = None
+    L.or14_flux_given_closure.argtypes = [_dp, _dp, _dp, _dp, C.c_int, _dp]
+    L.or14_flux_given_closure.restype = None
+    L.or14_flux.argtypes = [_dp, C.c_double, C.c_int, _dp]; L.or14_flux.restype = None
+    L.or14_lambda_star_max.argtypes = [C.c_double] * 4
+    L.or14_lambda_star_max.restype = C.c_double
+    L.or14_wavespeeds.argtypes = [_dp, C.c_int, C.c_double, C.c_double,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.or14_wavespeeds.restype = None
+    L.or14_source.argtypes = [_dp, C.c_double, _dp]; L.or14_source.restype = None
+    L.or_block_step.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
+                                _dp, C.c_double, _dp]
+    L.or_block_step.restype = C.c_int
+    L.or_block_residual.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, C.c_int,
+                                    _dp, _dp]
+    L.or_block_residual.restype = C.c_int
+    L.or_max_rate.argtypes = [C.POINTER(Cfg), _dp]; L.or_max_rate.restype = C.c_double
+    L.or_dt.argtypes = [C.POINTER(Cfg), _dp, C.c_double, C.c_double]
+    L.or_dt.restype = C.c_double
+    L.or_step.argtypes = [C.POINTER(Cfg), _dp, C.c_double]; L.or_step.restype = C.c_int
+    L.or_run.argtypes = [C.POINTER(Cfg), _dp, C.POINTER(C.c_double), C.c_double,
+                         C.c_int, C.c_void_p]
+    L.or_run.restype = C.c_int
+    L.or_tau.argtypes = [C.POINTER(Cfg), _dp]; L.or_tau.restype = C.c_double
+    L.or_prim2cons_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_prim2cons_n.restype = None
+    L.or_cons2prim_n.argtypes = [C.c_int, C.c_long, _dp, _dp]; L.or_cons2prim_n.restype = None
+    L.or_threads.argtypes = []; L.or_threads.restype = C.c_int
+    return L
 
 
 def _a(x, n=None):
@@ -265,30 +293,30 @@ def nf_of(cfg: Cfg) -> int:
     return 5 if cfg.system == 5 else 14
 
 
-def max_rate(cfg: Cfg, U):
+def max_rate(cfg: Cfg, U, omp=False):
     """U: (ny, nx, nf) conserved, interior cells."""
-    return lib().or_max_rate(C.byref(cfg), _a(U).reshape(-1))
+    return (lib_omp() if omp else lib()).or_max_rate(C.byref(cfg), _a(U).reshape(-1))
 
 
-def dt(cfg: Cfg, U, t, t_end):
-    return lib().or_dt(C.byref(cfg), _a(U).reshape(-1), t, t_end)
+def dt(cfg: Cfg, U, t, t_end, omp=False):
+    return (lib_omp() if omp else lib()).or_dt(C.byref(cfg), _a(U).reshape(-1), t, t_end)
 
 
-def step(cfg: Cfg, U, dtv):
+def step(cfg: Cfg, U, dtv, omp=False):
     """Advance U (ny, nx, nf) by one step of size dt; returns a new array."""
     out = np.array(U, dtype=np.float64, order="C", copy=True)
     flat = out.reshape(-1)
-    rc = lib().or_step(C.byref(cfg), flat, dtv)
+    rc = (lib_omp() if omp else lib()).or_step(C.byref(cfg), flat, dtv)
     assert rc == 0
     return out
 
 
-def run(cfg: Cfg, U, t, t_end, max_steps):
+def run(cfg: Cfg, U, t, t_end, max_steps, omp=False):
     out = np.array(U, dtype=np.float64, order="C", copy=True)
     tt = C.c_double(t)
     hist = np.zeros(max(max_steps, 1))
-    n = lib().or_run(C.byref(cfg), out.reshape(-1), C.byref(tt), t_end, max_steps,
-                     hist.ctypes.data_as(C.c_void_p))
+    n = (lib_omp() if omp else lib()).or_run(C.byref(cfg), out.reshape(-1), C.byref(tt), t_end,
+                                             max_steps, hist.ctypes.data_as(C.c_void_p))
     return out, tt.value, hist[:n]
 
 

@@ -31,6 +31,24 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Timing build (-fopenmp): the loops over rows, columns and cells of the
+ * scheme run on all host cores.  Every cell's arithmetic and the order of
+ * the contributions to it are those of the serial build, so both builds
+ * give bitwise equal results; without -fopenmp the macros are empty. */
+#if defined(_OPENMP) && !defined(__cplusplus)
+#include <omp.h>
+#define OR_PRAGMA(x) _Pragma(#x)
+#define OR_PARALLEL_FOR OR_PRAGMA(omp parallel for schedule(static))
+#define OR_PARALLEL_FOR_MAX(v) OR_PRAGMA(omp parallel for schedule(static) reduction(max : v))
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+#define OR_PARALLEL_FOR
+#define OR_PARALLEL_FOR_MAX(v)
+#ifndef __cplusplus
+int or_threads(void) { return 1; }
+#endif
+#endif
+
 /* Arithmetic type of every moment and derived quantity: double.  The
  * oracle's forward-mode tangent (tangent.cpp) compiles this same file with
  * a dual-number type in its place; nothing else changes. */
@@ -825,12 +843,14 @@ static void residual_region(const or_cfg *c, const blk *b, real *A,
     real dy = (c->y1 - c->y0) / c->ny;
     size_t ncell = (size_t)b->W * b->H;
     real *Qp = (real *)malloc(ncell * nf * sizeof(real));
+    OR_PARALLEL_FOR
     for (size_t n = 0; n < ncell; ++n) {
         if (!isnan(b->gp[n * nf])) memcpy(Qp + n * nf, b->gp + n * nf, nf * sizeof(real));
         else cons2prim(c, A + n * nf, Qp + n * nf);
     }
     int rw = xb - xa;
     /* L[(j-ya)*rw + (i-xa)] */
+    OR_PARALLEL_FOR
     for (int j = ya; j < yb; ++j)
         for (int i = xa; i < xb; ++i) {
             real *Lc = L + ((size_t)(j - ya) * rw + (i - xa)) * nf;
@@ -843,47 +863,47 @@ static void residual_region(const or_cfg *c, const blk *b, real *A,
             for (int k = 0; k < nf; ++k) Lc[k] = C[k];
         }
     int ndim = (c->ny == 1) ? 1 : 2;
-    real *Fm = (real *)malloc((size_t)nf * sizeof(real));
+    int rh = yb - ya;
     for (int d = 0; d < ndim; ++d) {
         real h = (d == 0) ? dx : dy;
-        /* faces along lines: face between cell a = s-1 and b = s, s in [lo, hi] */
-        if (d == 0) {
-            for (int j = ya; j < yb; ++j) {
-                real Fprev[14];
-                for (int s = xa; s <= xb; ++s) {
-                    real QL[14], QR[14], F[14];
-                    face_state(c, cell(b, Qp, s - 2, j), cell(b, Qp, s - 1, j),
-                               cell(b, Qp, s, j), +1.0, QL);
-                    face_state(c, cell(b, Qp, s - 1, j), cell(b, Qp, s, j),
-                               cell(b, Qp, s + 1, j), -1.0, QR);
-                    face_flux(c, QL, QR, 0, F);
-                    if (s > xa) {
-                        real *Lc = L + ((size_t)(j - ya) * rw + (s - 1 - xa)) * nf;
-                        for (int k = 0; k < nf; ++k) Lc[k] -= (F[k] - Fprev[k]) / h;
-                    }
-                    memcpy(Fprev, F, sizeof(real) * nf);
-                }
+        /* face s of a line lies between cells s-1 and s; a line of the
+         * region has nfl faces (rw + 1 along x, rh + 1 along y), and there
+         * are nl lines (rh rows, or rw columns).  All face fluxes first,
+         * then the flux differences, line by line in face order. */
+        int nfl = (d == 0) ? rw + 1 : rh + 1;
+        int nl = (d == 0) ? rh : rw;
+        real *F = (real *)malloc((size_t)nl * nfl * nf * sizeof(real));
+        OR_PARALLEL_FOR
+        for (long f = 0; f < (long)nl * nfl; ++f) {
+            int l = (int)(f / nfl), s = (int)(f % nfl);
+            real QL[14], QR[14];
+            if (d == 0) {
+                int j = ya + l, si = xa + s;
+                face_state(c, cell(b, Qp, si - 2, j), cell(b, Qp, si - 1, j),
+                           cell(b, Qp, si, j), +1.0, QL);
+                face_state(c, cell(b, Qp, si - 1, j), cell(b, Qp, si, j),
+                           cell(b, Qp, si + 1, j), -1.0, QR);
+            } else {
+                int i = xa + l, sj = ya + s;
+                face_state(c, cell(b, Qp, i, sj - 2), cell(b, Qp, i, sj - 1),
+                           cell(b, Qp, i, sj), +1.0, QL);
+                face_state(c, cell(b, Qp, i, sj - 1), cell(b, Qp, i, sj),
+                           cell(b, Qp, i, sj + 1), -1.0, QR);
             }
-        } else {
-            for (int i = xa; i < xb; ++i) {
-                real Fprev[14];
-                for (int s = ya; s <= yb; ++s) {
-                    real QL[14], QR[14], F[14];
-                    face_state(c, cell(b, Qp, i, s - 2), cell(b, Qp, i, s - 1),
-                               cell(b, Qp, i, s), +1.0, QL);
-                    face_state(c, cell(b, Qp, i, s - 1), cell(b, Qp, i, s),
-                               cell(b, Qp, i, s + 1), -1.0, QR);
-                    face_flux(c, QL, QR, 1, F);
-                    if (s > ya) {
-                        real *Lc = L + ((size_t)(s - 1 - ya) * rw + (i - xa)) * nf;
-                        for (int k = 0; k < nf; ++k) Lc[k] -= (F[k] - Fprev[k]) / h;
-                    }
-                    memcpy(Fprev, F, sizeof(real) * nf);
-                }
-            }
+            face_flux(c, QL, QR, d, F + (size_t)f * nf);
         }
+        OR_PARALLEL_FOR
+        for (int l = 0; l < nl; ++l)
+            for (int s = 1; s < nfl; ++s) {
+                const real *Fr = F + ((size_t)l * nfl + s) * nf;
+                const real *Fl = Fr - nf;
+                /* cell s-1 of line l */
+                real *Lc = (d == 0) ? L + ((size_t)l * rw + (s - 1)) * nf
+                                    : L + ((size_t)(s - 1) * rw + l) * nf;
+                for (int k = 0; k < nf; ++k) Lc[k] -= (Fr[k] - Fl[k]) / h;
+            }
+        free(F);
     }
-    free(Fm);
     free(Qp);
 }
 
@@ -930,6 +950,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
     if (c->integrator == OR_FE) {
         real *L = (real *)malloc((size_t)w * h * nf * sizeof(real));
         residual_region(c, &b, A, 0, w, 0, h, L);
+        OR_PARALLEL_FOR
         for (int j = 0; j < h; ++j)
             for (int i = 0; i < w; ++i) {
                 real *Uc = cell(&b, A, i, j);
@@ -956,6 +977,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
     residual_region(c, &b, A, xa, xb, ya, yb, L);
     real *S = (real *)malloc(n * sizeof(real));
     memcpy(S, A, n * sizeof(real));
+    OR_PARALLEL_FOR
     for (int j = ya; j < yb; ++j)
         for (int i = xa; i < xb; ++i) {
             real *Uc = cell(&b, A, i, j);
@@ -967,6 +989,7 @@ int or_block_step(const or_cfg *c, int i0, int j0, int w, int h,
     fill_bc(c, &b, S);
     real *L2 = (real *)malloc((size_t)w * h * nf * sizeof(real));
     residual_region(c, &b, S, 0, w, 0, h, L2);
+    OR_PARALLEL_FOR
     for (int j = 0; j < h; ++j)
         for (int i = 0; i < w; ++i) {
             real *Uc = cell(&b, A, i, j);
@@ -991,6 +1014,7 @@ real or_max_rate(const or_cfg *c, const real *U) {
     real dy = (c->y1 - c->y0) / c->ny;
     int ndim = (c->ny == 1) ? 1 : 2;
     real m = 0.0;
+    OR_PARALLEL_FOR_MAX(m)
     for (size_t n = 0; n < (size_t)c->nx * c->ny; ++n) {
         real Q[14];
         cons2prim(c, U + n * nf, Q);
