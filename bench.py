@@ -65,6 +65,8 @@ def parse():
                    help="timed steps of the other precision")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--scalar-faces", action="store_true",
+                   help="planar mixed stage: scalar face states instead of packed FP32 pairs")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-tube leg (256 Sod tubes, one graph launch)")
@@ -505,6 +507,8 @@ def main():
     def timed(precision, steps, sample_clocks):
         s = make_solver(mx, wl, n, precision, setup)
         s.set_stream(stream.cuda_stream)
+        if precision == "mixed" and args.scalar_faces:
+            s.set_face_packing(False)
         s.set_state(prim)
         for _ in range(args.warmup):
             s.step(1, float("inf"), sync=False)

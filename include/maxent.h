@@ -209,6 +209,18 @@ mxe_status mxe_set_mixed_policy(mxe_ctx *ctx, double sigma_lo, double sigma_hi,
  * context. */
 mxe_status mxe_set_stage_occupancy(mxe_ctx *ctx, int blocks_per_sm);
 
+/* 2D MXE_MIXED only, planar states at three blocks per SM: how the two face
+ * states of a face are evaluated (closure Eqs. closure-14mom-Qijk/Rijkk/
+ * Sijjkk, wave speeds Eq. 14mom-approx-ws-equations, Sec. 3.1 flux).
+ * packed = 1 (default): as one pair in packed FP32 (f32x2) arithmetic, the
+ * left state in one lane and the right state in the other; a face whose
+ * closure is ill-conditioned in either state (mxe_set_mixed_policy) takes
+ * both states in FP64.  packed = 0: one state after the other in scalar
+ * FP32, only the ill-conditioned state in FP64.  The two agree to FP32
+ * rounding.  MXE_EINVAL for another value, MXE_ESTATE on another kind of
+ * context. */
+mxe_status mxe_set_face_packing(mxe_ctx *ctx, int packed);
+
 /* Diagnostics of the current state (synchronises). */
 mxe_status mxe_get_diagnostics(mxe_ctx *ctx, mxe_diag *out);
 

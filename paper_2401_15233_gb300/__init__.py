@@ -27,6 +27,7 @@ __all__ = [
     "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
     "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual", "mxe_set_adjoint_precision",
     "mxe_set_stage_occupancy", "mxe_set_source_scheme", "mxe_set_adjoint_limiter",
+    "mxe_set_face_packing",
 ]
 
 SOURCE_EXPLICIT, SOURCE_POINT_IMPLICIT = 0, 1
@@ -119,6 +120,7 @@ def lib():
             "mxe_adjoint_residual": ([_P, _P, _P, _P, C.c_int, _P, _P], C.c_int),
             "mxe_set_mixed_policy": ([_P, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
             "mxe_set_stage_occupancy": ([_P, C.c_int], C.c_int),
+            "mxe_set_face_packing": ([_P, C.c_int], C.c_int),
             "mxe_set_source_scheme": ([_P, C.c_int], C.c_int),
             "mxe_set_adjoint_limiter": ([_P, C.c_int], C.c_int),
             "mxe_tube_run_noalloc": ([C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_double,
@@ -268,6 +270,10 @@ def mxe_set_source_scheme(ctx, scheme):
 
 def mxe_set_stage_occupancy(ctx, blocks_per_sm):
     _check(ctx, lib().mxe_set_stage_occupancy(ctx, blocks_per_sm))
+
+
+def mxe_set_face_packing(ctx, packed):
+    _check(ctx, lib().mxe_set_face_packing(ctx, int(packed)))
 
 
 def mxe_tube_run_noalloc(cfg: Config, U_dev, t0, t_end, max_steps, bc_lo=BC_TRANSMISSIVE,
@@ -479,6 +485,11 @@ class Solver:
     def set_stage_occupancy(self, blocks_per_sm):
         """Planar mixed stage kernel: 3 (default) or 2 blocks per SM."""
         mxe_set_stage_occupancy(self.ctx, blocks_per_sm)
+
+    def set_face_packing(self, packed):
+        """Planar mixed stage at 3 blocks per SM: True (default) evaluates
+        the two face states of a face as one packed FP32 pair."""
+        mxe_set_face_packing(self.ctx, packed)
 
 
 class Batch(Solver):

@@ -40,6 +40,9 @@ extern "C" __global__ void mxe_stage14_2d_mixed_b3(const Stage2DArgs a, const Pa
 extern "C" __global__ void mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a,
                                                           const ParamsT<float> p,
                                                           const MixedPolicy mp);
+extern "C" __global__ void mxe_stage14_2d_mixed_planar_x2(const Stage2DArgs a,
+                                                          const ParamsT<float> p,
+                                                          const MixedPolicy mp);
 extern "C" __global__ void mxe_resync14_2d(const double* U, float* W, Grid2D g);
 extern "C" __global__ void mxe_resync14_2d_planar(const double* U, float* W, Grid2D g);
 extern "C" __global__ void mxe_rate14_2d_mixed(const float* W, Grid2D g, ParamsT<float> p,
@@ -134,6 +137,7 @@ struct mxe_ctx {
     MixedPolicy mp{0.0f, 0.999f, 1e-3f};
     int resync_every = 16;
     int stage_occ = 3;                // mixed stage kernels: blocks per SM (2 or 3)
+    int face_packed = 1;              // planar mixed, 3 blocks/SM: face-state pairs in f32x2
     long long launched = 0;           // steps launched since set_state
     bool state_planar = false;        // z-odd moments exactly zero (and kept so)
     bool w_planar = false;            // layout of W (mixed): compact planar fields
@@ -358,6 +362,10 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
                                                 (int)stage14_2d_f64_smem(true));
         if (e == cudaSuccess && c->mixed)
             e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar_b3,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)stage14_2d_mixed_smem(true, 3));
+        if (e == cudaSuccess && c->mixed)
+            e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar_x2,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)stage14_2d_mixed_smem(true, 3));
         if (e == cudaSuccess && c->mixed)
@@ -762,7 +770,9 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
         // three blocks per SM (L2 prefetch) or two (planar: with the final
         // stage's shared-memory prefetch); the same kernel for both stages
         const bool b3 = c->stage_occ == 3;
-        const auto kern = pl ? (b3 ? mxe_stage14_2d_mixed_planar_b3 : mxe_stage14_2d_mixed_planar)
+        const auto kern = pl ? (b3 ? (c->face_packed ? mxe_stage14_2d_mixed_planar_x2
+                                                     : mxe_stage14_2d_mixed_planar_b3)
+                                   : mxe_stage14_2d_mixed_planar)
                              : (b3 ? mxe_stage14_2d_mixed_b3 : mxe_stage14_2d_mixed);
         const size_t smem = stage14_2d_mixed_smem(pl, c->stage_occ);
         ParamsT<float> fp = fparams(c);
@@ -1101,6 +1111,14 @@ extern "C" mxe_status mxe_set_stage_occupancy(mxe_ctx* c, int blocks_per_sm) {
     if (blocks_per_sm != 2 && blocks_per_sm != 3)
         return fail(c, MXE_EINVAL, "blocks_per_sm must be 2 or 3");
     c->stage_occ = blocks_per_sm;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_set_face_packing(mxe_ctx* c, int packed) {
+    if (!c) return MXE_EINVAL;
+    if (!c->mixed || c->tubes) return fail(c, MXE_ESTATE, "not a 2D MXE_MIXED context");
+    if (packed != 0 && packed != 1) return fail(c, MXE_EINVAL, "packed must be 0 or 1");
+    c->face_packed = packed;
     return MXE_OK;
 }
 

@@ -23,6 +23,7 @@
 // planar (ten-moment) state.
 #include "mxe_internal.h"
 #include "mxe_mixed.cuh"
+#include "mxe_planar_x2.cuh"
 
 namespace mxe {
 
@@ -159,6 +160,113 @@ __device__ __forceinline__ void face_flux_m(const float* W, int cl, int cr, int 
     }
 }
 
+// FP64 face flux of a face whose packed FP32 evaluation found an
+// ill-conditioned closure in either face state: both states are evaluated
+// again in FP64 (kept out of line and called with the two input states by
+// value, so that nothing else is live across the call).
+template <int NF>
+struct FacePairIn {
+    float q[2 * NF];
+};
+template <int NF>
+struct FaceFluxOut {
+    float f[NF];
+};
+template <int K>
+__device__ __noinline__ FaceFluxOut<NP> face_flux_fp64(FacePairIn<NP> in, double sl, double kw,
+                                                       int flux) {
+    constexpr int NF = NP;
+    double QL[NF], QR[NF], UL[NF], UR[NF], FL[NF], FR[NF], lminL, lmaxL, lminR, lmaxR;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        QL[k] = (double)in.q[k];
+        QR[k] = (double)in.q[NF + k];
+    }
+    PhysPlanar::face<double, K>(QL, sl, kw, UL, FL, lminL, lmaxL);
+    PhysPlanar::face<double, K>(QR, sl, kw, UR, FR, lminR, lmaxR);
+    FaceFluxOut<NF> r;
+    if (flux == 1) {
+        double sp = fmax(fmax(fabs(lminL), fabs(lmaxL)), fmax(fabs(lminR), fabs(lmaxR)));
+#pragma unroll
+        for (int k = 0; k < NF; ++k) r.f[k] = (float)(0.5 * (FL[k] + FR[k]) - 0.5 * sp * (UR[k] - UL[k]));
+        return r;
+    }
+    double SL = fmin(lminL, lminR), SR = fmax(lmaxL, lmaxR);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        double f;
+        if (SL >= 0.0) f = FL[k];
+        else if (SR <= 0.0) f = FR[k];
+        else f = (SR * FL[k] - SL * FR[k] + SL * SR * (UR[k] - UL[k])) / (SR - SL);
+        r.f[k] = (float)f;
+    }
+    return r;
+}
+
+// Both face states of the face between box cells cl and cl + stride along K
+// (planar state), evaluated as one packed FP32 pair (left state in lane x,
+// right in lane y): the reconstruction shares the four stencil cells, and
+// no face state is staged in shared memory.  A face with an ill-conditioned
+// closure in either state (the policy of face_state_m) takes its flux from
+// face_flux_fp64 instead.
+template <int K>
+__device__ __forceinline__ void face_flux_x2(const float* W, int cl, int stride, float phl,
+                                             float phr, const ParamsT<float>& p,
+                                             const MixedPolicy& mp, double sl64, double kw64,
+                                             float* F, unsigned& nflag) {
+    using namespace x2;
+    constexpr int NF = NP;
+    v2 Q[NF];
+    const v2 hp = make_float2(0.25f * phl, -0.25f * phr);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        const float* w = W + k * NBOXm + cl;
+        const float wm = w[-stride], w0 = w[0], w1 = w[stride], w2 = w[2 * stride];
+        Q[k] = fma(hp, sub(make_float2(w1, w2), make_float2(wm, w0)), make_float2(w0, w1));
+    }
+    v2 U[NF], Fv[NF], lmin, lmax, sig, det;
+    face_eval_x2<K>(Q, p.sigma_lim, p.k_ws, U, Fv, lmin, lmax, sig, det);
+    if (p.flux == 1) {
+        float s = fmaxf(fmaxf(fabsf(lmin.x), fabsf(lmax.x)), fmaxf(fabsf(lmin.y), fabsf(lmax.y)));
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+            F[k] = 0.5f * (Fv[k].x + Fv[k].y) - 0.5f * s * (U[k].y - U[k].x);
+    } else {
+        float SL = fminf(lmin.x, lmin.y), SR = fmaxf(lmax.x, lmax.y);
+        if (SL >= 0.0f) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) F[k] = Fv[k].x;
+        } else if (SR <= 0.0f) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) F[k] = Fv[k].y;
+        } else {
+            float inv = 1.0f / (SR - SL);
+            float cl_ = SR * inv, cr_ = -SL * inv, cu = SL * SR * inv;
+#pragma unroll
+            for (int k = 0; k < NF; ++k)
+                F[k] = cl_ * Fv[k].x + cr_ * Fv[k].y + cu * (U[k].y - U[k].x);
+        }
+    }
+    if (mp.sig_lo > 0.0f || mp.sig_hi < 1.0f || mp.det_min > 0.0f) {
+        const bool fx = (sig.x >= p.sigma_lim && sig.x < mp.sig_lo) || sig.x > mp.sig_hi ||
+                        det.x < mp.det_min || !(sig.x == sig.x);
+        const bool fy = (sig.y >= p.sigma_lim && sig.y < mp.sig_lo) || sig.y > mp.sig_hi ||
+                        det.y < mp.det_min || !(sig.y == sig.y);
+        nflag += (fx ? 1u : 0u) + (fy ? 1u : 0u);
+        if (__any_sync(__activemask(), fx || fy) && (fx || fy)) {
+            FacePairIn<NF> in;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                in.q[k] = Q[k].x;
+                in.q[NF + k] = Q[k].y;
+            }
+            FaceFluxOut<NF> r = face_flux_fp64<K>(in, sl64, kw64, p.flux);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) F[k] = r.f[k];
+        }
+    }
+}
+
 __device__ __forceinline__ void block_max_atomic_m(float r, unsigned long long* dst, float* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
@@ -211,7 +319,7 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 }
 
 
-template <class PH, bool PFON>
+template <class PH, bool PFON, bool X2 = false>
 __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<float>& p,
                                             const MixedPolicy& mp) {
     constexpr int NF = PH::NF;
@@ -308,15 +416,26 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
     {   // x face tid, then y face tid (no barrier in between)
         int fx = tid & 15, fcy = tid >> 4, by = fcy + 2;
         float F[NF];
-        face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1, phx[fcy * (TXm + 2) + fx],
-                           phx[fcy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, Ls + tid, F, nflag);
+        if constexpr (X2) {
+            face_flux_x2<0>(W, by * BXm + fx + 1, 1, phx[fcy * (TXm + 2) + fx],
+                            phx[fcy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, F, nflag);
+        } else {
+            face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1,
+                               phx[fcy * (TXm + 2) + fx], phx[fcy * (TXm + 2) + fx + 1], p, mp,
+                               sl64, kw64, Ls + tid, F, nflag);
+        }
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fx[k * NTm + tid] = F[k];
         if (tid < TXm * (TYm + 1)) {
             int fcx = tid % TXm, fy = tid / TXm, bx = fcx + 2;
-            face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm,
-                               phy[fy * TXm + fcx], phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64,
-                               Ls + tid, F, nflag);
+            if constexpr (X2) {
+                face_flux_x2<1>(W, (fy + 1) * BXm + bx, BXm, phy[fy * TXm + fcx],
+                                phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64, F, nflag);
+            } else {
+                face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm,
+                                   phy[fy * TXm + fcx], phy[(fy + 1) * TXm + fcx], p, mp, sl64,
+                                   kw64, Ls + tid, F, nflag);
+            }
 #pragma unroll
             for (int k = 0; k < NF; ++k) Fy[k * NTm + tid] = F[k];
         }
@@ -436,6 +555,14 @@ extern "C" __global__ void __launch_bounds__(NTm, 3)
 mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a, const ParamsT<float> p,
                                const MixedPolicy mp) {
     stage_mixed<PhysPlanar, false>(a, p, mp);
+}
+
+// planar state at three blocks per SM with both face states of a face
+// evaluated as one packed FP32 pair (the default for planar states)
+extern "C" __global__ void __launch_bounds__(NTm, 3)
+mxe_stage14_2d_mixed_planar_x2(const Stage2DArgs a, const ParamsT<float> p,
+                               const MixedPolicy mp) {
+    stage_mixed<PhysPlanar, false, true>(a, p, mp);
 }
 
 size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm) {

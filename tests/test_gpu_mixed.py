@@ -187,7 +187,7 @@ def test_mixed_sampled_4096_bench_config(mx, orc):
 @pytest.mark.parametrize("uz", [0.0, 0.8])
 def test_stage_occupancy_same_result(mx, uz):
     """The stage kernels at two blocks per SM and at three (80 registers, L2
-    prefetch) run the same source: each variant is bitwise reproducible from
+    prefetch) run the same source (scalar face states): each variant is bitwise reproducible from
     run to run, and the two agree bitwise for the planar state.  For the
     general state the two builds differ in FP32 rounding (the compiler fuses
     a different set of multiply-add pairs under the two register budgets):
@@ -202,6 +202,7 @@ def test_stage_occupancy_same_result(mx, uz):
     for occ in (2, 3, 3):
         s = jets_gpu_solver(mx, n, n, setup, precision="mixed")
         s.set_stage_occupancy(occ)
+        s.set_face_packing(False)          # the same scalar face arithmetic at both shapes
         s.set_state(prim)
         s.step(20, float("inf"))
         res = (s.get_moments("conserved"), s.diagnostics()["t"])
@@ -265,3 +266,48 @@ def test_mixed_l1_bench_size_against_fp64(mx):
     print("4096^2, 20 steps: mixed L1", e.max(), "sensitivity", sens.max())
     nz = np.abs(A).reshape(14, -1).sum(1) > 0
     assert np.all(e[nz] <= np.maximum(10 * sens[nz], 1e-10)), (e, sens)
+
+
+@pytest.mark.parametrize("flux", ["hll", "rusanov"])
+def test_face_packing_agrees_with_scalar(mx, orc, flux):
+    """Packed FP32 pairs of face states (the default for planar states at
+    three blocks per SM) against one-state-at-a-time scalar FP32: the same
+    formulas regrouped into fused multiply-adds, so one step from the
+    oracle's state differs by FP32 rounding only.  Each variant is bitwise
+    reproducible and within the mixed per-step bound (1e-4) of the FP64
+    oracle, and the packed error is no larger than 1.5x the scalar one
+    (measured: 2.6e-5 against 2.3e-5; the FP32 input state dominates both)."""
+    from tests.test_gpu_implicit import fam_err
+    n = 96
+    setup = wl.jets_setup(Kn=0.1)
+    prim = wl.jets_like_field(n, n, setup)
+    cfg = jets_oracle_cfg(orc, n, n, setup, flux=1 if flux == "rusanov" else 0)
+    U = cons_field(orc, prim)
+    dt = orc.dt(cfg, U, 0.0, 10.0)
+    ref = orc.step(cfg, U, dt)
+    out = {}
+    for packed, policy in ((True, "default"), (False, "default"), (True, "default"),
+                           (True, "all"), (False, "all")):
+        s = jets_gpu_solver(mx, n, n, setup, precision="mixed", flux=flux)
+        s.set_face_packing(packed)
+        s.set_mixed_policy(*POLICIES[policy], resync_every=16)
+        s.set_state(aos_to_soa(U), kind="conserved")
+        s.step_dt([dt])
+        got = soa_to_aos(s.get_moments("conserved"))
+        if (packed, policy) in out:
+            assert np.array_equal(got, out[(packed, policy)])
+        out[(packed, policy)] = got
+        e = fam_err(got, ref)
+        print(f"{flux} packed={packed} policy={policy}: vs oracle {e.max():.2e}")
+        assert e.max() <= 1e-4
+    err = {k: fam_err(v, ref).max() for k, v in out.items()}
+    d = fam_err(out[(True, "default")], out[(False, "default")])
+    print(f"{flux}: packed vs scalar {d.max():.2e}")
+    assert err[(True, "default")] <= 1.5 * err[(False, "default")]
+    assert err[(True, "all")] <= 1.5 * err[(False, "all")]
+    s = jets_gpu_solver(mx, 16, 16, setup, precision="mixed")
+    with pytest.raises(mx.MaxentError):
+        s.set_face_packing(2)
+    f = jets_gpu_solver(mx, 16, 16, setup, precision="fp64")
+    with pytest.raises(mx.MaxentError):
+        f.set_face_packing(True)
