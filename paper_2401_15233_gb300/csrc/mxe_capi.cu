@@ -51,6 +51,9 @@ extern "C" __global__ void mxe_rate14_2d_mixed_planar(const float* W, Grid2D g,
                                                       ParamsT<float> p, float idxf, float idyf,
                                                       DevClock* clk, int slot);
 size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm);
+size_t stage14_2d_mixed_x2_smem();
+int stage14_2d_mixed_x2_tile_x();
+int stage14_2d_mixed_x2_tile_y();
 const void* tubes_mixed_kernel(bool planar, int nt);
 cudaError_t adj_stage(const double* U, const double* V, double coef, const double* b1,
                       const double* b2, double* out, double* P, double* Cx, double* Cy,
@@ -367,7 +370,7 @@ extern "C" mxe_status mxe_create(const mxe_config* cfg, mxe_ctx** out) {
         if (e == cudaSuccess && c->mixed)
             e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_planar_x2,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)stage14_2d_mixed_smem(true, 3));
+                                     (int)stage14_2d_mixed_x2_smem());
         if (e == cudaSuccess && c->mixed)
             e = cudaFuncSetAttribute(mxe_stage14_2d_mixed_b3,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -770,23 +773,32 @@ static mxe_status launch_2d_step(mxe_ctx* c, double t_end, double dt_fixed,
         // three blocks per SM (L2 prefetch) or two (planar: with the final
         // stage's shared-memory prefetch); the same kernel for both stages
         const bool b3 = c->stage_occ == 3;
-        const auto kern = pl ? (b3 ? (c->face_packed ? mxe_stage14_2d_mixed_planar_x2
-                                                     : mxe_stage14_2d_mixed_planar_b3)
-                                   : mxe_stage14_2d_mixed_planar)
+        const bool packed = pl && b3 && c->face_packed;
+        const auto kern = pl ? (b3 ? mxe_stage14_2d_mixed_planar_b3 : mxe_stage14_2d_mixed_planar)
                              : (b3 ? mxe_stage14_2d_mixed_b3 : mxe_stage14_2d_mixed);
         const size_t smem = stage14_2d_mixed_smem(pl, c->stage_occ);
-        ParamsT<float> fp = fparams(c);
+        // packed planar stage: its own kernel and tile
+        auto launch = [&]() {
+            if (!packed) {
+                kern<<<grid, 256, smem, c->stream>>>(a, fparams(c), c->mp);
+                return;
+            }
+            const int tx = stage14_2d_mixed_x2_tile_x(), ty = stage14_2d_mixed_x2_tile_y();
+            dim3 gp((c->g.nx + tx - 1) / tx, (c->g.ny + ty - 1) / ty);
+            mxe_stage14_2d_mixed_planar_x2<<<gp, 256, stage14_2d_mixed_x2_smem(), c->stream>>>(
+                a, fparams(c), c->mp);
+        };
         a.Ubase = c->U;
         a.Uout = c->U;
         a.resync = (c->launched + 1) % c->resync_every == 0;
         if (c->cfg.integrator == MXE_RK2) {
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 0.5; a.final_stage = 0;
-            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
+            launch();
             a.Win = c->Ws; a.Wout = c->W; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
+            launch();
         } else {
             a.Win = c->W; a.Wout = c->Ws; a.Wbase = c->W; a.coef = 1.0; a.final_stage = 1;
-            kern<<<grid, 256, smem, c->stream>>>(a, fp, c->mp);
+            launch();
             std::swap(c->W, c->Ws);
         }
         CK(cudaGetLastError());

@@ -107,6 +107,65 @@ __device__ __forceinline__ float phi_box_m(const float* W, int c, int stride, in
     return phi;
 }
 
+// One field's contribution to the shared limiter of one direction, tracked
+// as the ratio r = min(|dm|, |dp|) / max(|dm|, |dp|) of the most stringent
+// field so far (n / x).  Both limiters are increasing in r on [0, 1]
+// (minmod 2r/(1+r), van Albada 2r/(1+r^2)), so the field with the smallest
+// r sets phi, and ratios are compared cross-multiplied: one division per
+// cell and direction instead of one per field.  Opposite signs give r = 0;
+// a field with dm = dp = 0, or flat by the tolerance test, never lowers phi.
+template <int NF>
+__device__ __forceinline__ void phi_ratio_step(float dm, float dp, float w0,
+                                               const FlatRef<float>& fr, int k, float& n,
+                                               float& x) {
+    const float am = fabsf(dm), ap = fabsf(dp);
+    const float mx = fmaxf(am, ap);
+    const float mn = dm * dp > 0.0f ? fminf(am, ap) : 0.0f;
+    if (mx > 0.0f && mn * x < n * mx) {
+        if (!(mx <= FLAT_REL_F32 * fabsf(w0) || field_flat<NF>(fr, k, mx))) {
+            n = mn;
+            x = mx;
+        }
+    }
+}
+__device__ __forceinline__ float phi_of_ratio(float n, float x, int lim) {
+    return lim == 1 ? __fdividef(2.0f * n * x, n * n + x * x) : __fdividef(2.0f * n, n + x);
+}
+
+// Shared limiter of box cell c in x (result .x) and y (.y): the stencil
+// centre and the flat-test reference are loaded once for both directions.
+template <int NF, int NBOX, int BX>
+__device__ __forceinline__ float2 phi_pair_m(const float* W, int c, int lim) {
+    using namespace x2;
+    const FlatRef<float> fr = flat_ref<NF>(W + c, NBOX);
+    float nx = 1.0f, xx = 1.0f, ny = 1.0f, xy = 1.0f;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        const float* w = W + k * NBOX + c;
+        const float w0 = w[0];
+        // the x and y differences as the lanes of packed subtractions
+        const v2 dm = sub(S(w0), make_float2(w[-1], w[-BX]));
+        const v2 dp = sub(make_float2(w[1], w[BX]), S(w0));
+        phi_ratio_step<NF>(dm.x, dp.x, w0, fr, k, nx, xx);
+        phi_ratio_step<NF>(dm.y, dp.y, w0, fr, k, ny, xy);
+    }
+    return make_float2(phi_of_ratio(nx, xx, lim), phi_of_ratio(ny, xy, lim));
+}
+
+// The same for one direction (stride 1: x, stride BX: y).
+template <int NF, int NBOX>
+__device__ __forceinline__ float phi_one_m(const float* W, int c, int stride, int lim) {
+    const FlatRef<float> fr = flat_ref<NF>(W + c, NBOX);
+    float n = 1.0f, x = 1.0f;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        const float* w = W + k * NBOX + c;
+        const float w0 = w[0];
+        phi_ratio_step<NF>(w0 - w[-stride], w[stride] - w0, w0, fr, k, n, x);
+    }
+    return phi_of_ratio(n, x, lim);
+}
+
 template <int NF>
 __device__ __forceinline__ void face_prims_m(const float* W, int c, int stride, float phi,
                                              float hs, float* Qf) {
@@ -209,7 +268,7 @@ __device__ __noinline__ FaceFluxOut<NP> face_flux_fp64(FacePairIn<NP> in, double
 // no face state is staged in shared memory.  A face with an ill-conditioned
 // closure in either state (the policy of face_state_m) takes its flux from
 // face_flux_fp64 instead.
-template <int K>
+template <int K, int NBOX>
 __device__ __forceinline__ void face_flux_x2(const float* W, int cl, int stride, float phl,
                                              float phr, const ParamsT<float>& p,
                                              const MixedPolicy& mp, double sl64, double kw64,
@@ -220,7 +279,7 @@ __device__ __forceinline__ void face_flux_x2(const float* W, int cl, int stride,
     const v2 hp = make_float2(0.25f * phl, -0.25f * phr);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const float* w = W + k * NBOXm + cl;
+        const float* w = W + k * NBOX + cl;
         const float wm = w[-stride], w0 = w[0], w1 = w[stride], w2 = w[2 * stride];
         Q[k] = fma(hp, sub(make_float2(w1, w2), make_float2(wm, w0)), make_float2(w0, w1));
     }
@@ -319,7 +378,7 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 }
 
 
-template <class PH, bool PFON, bool X2 = false>
+template <class PH, bool PFON>
 __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<float>& p,
                                             const MixedPolicy& mp) {
     constexpr int NF = PH::NF;
@@ -416,26 +475,15 @@ __device__ __forceinline__ void stage_mixed(const Stage2DArgs& a, const ParamsT<
     {   // x face tid, then y face tid (no barrier in between)
         int fx = tid & 15, fcy = tid >> 4, by = fcy + 2;
         float F[NF];
-        if constexpr (X2) {
-            face_flux_x2<0>(W, by * BXm + fx + 1, 1, phx[fcy * (TXm + 2) + fx],
-                            phx[fcy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, F, nflag);
-        } else {
-            face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1,
-                               phx[fcy * (TXm + 2) + fx], phx[fcy * (TXm + 2) + fx + 1], p, mp,
-                               sl64, kw64, Ls + tid, F, nflag);
-        }
+        face_flux_m<PH, 0>(W, by * BXm + fx + 1, by * BXm + fx + 2, 1, phx[fcy * (TXm + 2) + fx],
+                           phx[fcy * (TXm + 2) + fx + 1], p, mp, sl64, kw64, Ls + tid, F, nflag);
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fx[k * NTm + tid] = F[k];
         if (tid < TXm * (TYm + 1)) {
             int fcx = tid % TXm, fy = tid / TXm, bx = fcx + 2;
-            if constexpr (X2) {
-                face_flux_x2<1>(W, (fy + 1) * BXm + bx, BXm, phy[fy * TXm + fcx],
-                                phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64, F, nflag);
-            } else {
-                face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm,
-                                   phy[fy * TXm + fcx], phy[(fy + 1) * TXm + fcx], p, mp, sl64,
-                                   kw64, Ls + tid, F, nflag);
-            }
+            face_flux_m<PH, 1>(W, (fy + 1) * BXm + bx, (fy + 2) * BXm + bx, BXm,
+                               phy[fy * TXm + fcx], phy[(fy + 1) * TXm + fcx], p, mp, sl64, kw64,
+                               Ls + tid, F, nflag);
 #pragma unroll
             for (int k = 0; k < NF; ++k) Fy[k * NTm + tid] = F[k];
         }
@@ -557,13 +605,280 @@ mxe_stage14_2d_mixed_planar_b3(const Stage2DArgs a, const ParamsT<float> p,
     stage_mixed<PhysPlanar, false>(a, p, mp);
 }
 
-// planar state at three blocks per SM with both face states of a face
-// evaluated as one packed FP32 pair (the default for planar states)
-extern "C" __global__ void __launch_bounds__(NTm, 3)
+// Exact FP32 -> FP64 conversion by integer operations (GB300's FP64 pipe
+// retires 2 operations per clock per SM; a conversion there costs as much as
+// the accumulator add itself).  The exponent is re-biased by 1023 - 127 and
+// the mantissa shifted into place; zero and the values the FP32 stage flushes
+// to zero map to a signed zero, infinities and NaNs keep their class.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, em = b & 0x7fffffffu;
+    unsigned hi = sign | ((em >> 3) + (896u << 20));
+    unsigned lo = em << 29;
+    if (em < 0x00800000u) hi = sign, lo = 0u;                            // zero (FTZ)
+    if (em >= 0x7f800000u) hi = sign | 0x7ff00000u | ((em >> 3) & 0xfffffu);   // inf, NaN
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// ---------------------------------------------------------------------------
+// Packed planar stage (the default for planar states).  A block of NTP
+// threads owns a TX x TY tile; every thread evaluates two x faces and two y
+// faces as packed pairs of face states, the limiters of about two cells
+// (both directions of an interior cell in one evaluation), and updates two
+// cells.  The taller tile halves the halo cells loaded, the limiters
+// evaluated and the faces computed twice per owned cell, and the per-block
+// fixed work, against the 15 x 16 tile of the scalar kernels.
+template <int TX_, int TY_>
+struct TileGeo {
+    static constexpr int TX = TX_, TY = TY_;
+    static constexpr int BX = TX + 4, BY = TY + 4, NBOX = BX * BY;
+    static constexpr int NC = TX * TY;             // owned cells
+    static constexpr int NFX = (TX + 1) * TY;      // x faces
+    static constexpr int NFY = TX * (TY + 1);      // y faces
+    static constexpr int NPX = (TX + 2) * TY;      // x limiters
+    static constexpr int NPY = TX * (TY + 2);      // y limiters
+    // limiter work items: the owned cells (both directions), then the halo
+    // columns (x only) and the halo rows (y only)
+    static constexpr int NLIM = NC + 2 * TY + 2 * TX;
+};
+using TileP = TileGeo<15, 32>;
+constexpr int NTP = 256;
+static_assert(TileP::NFX <= 2 * NTP && TileP::NFY <= 2 * NTP && TileP::NC <= 2 * NTP,
+              "two faces per direction and two cells per thread");
+
+// shared memory of the packed stage: stencil box, x and y face fluxes,
+// limiters, reduction scratch
+template <class G>
+constexpr size_t smem_mixed_x2() {
+    return sizeof(float) * (NP * G::NBOX + NP * G::NFX + NP * G::NFY + G::NPX + G::NPY + 8);
+}
+
+template <class G>
+__device__ __forceinline__ void stage_mixed_x2(const Stage2DArgs& a, const ParamsT<float>& p,
+                                               const MixedPolicy& mp) {
+    using PH = PhysPlanar;
+    constexpr int NF = NP;
+    extern __shared__ __align__(16) double smd[];
+    float* W = (float*)smd;                          // [NF][BY][BX]
+    float* Fx = W + NF * G::NBOX;                    // [NF][TY][TX+1]
+    float* Fy = Fx + NF * G::NFX;                    // [NF][TY+1][TX]
+    float* phx = Fy + NF * G::NFY;                   // [TY][TX+2]
+    float* phy = phx + G::NPX;                       // [TY+2][TX]
+    float* red = phy + G::NPY;                       // [8]
+    __shared__ double sdt[2];
+    __shared__ float scdt;
+    __shared__ unsigned cnt;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        double tt;
+        sdt[0] = step_dt_m(a.clk, a.slot, a.cfl, a.t_end, a.dt_fixed, tt);
+        sdt[1] = tt;
+        scdt = (float)(a.coef * sdt[0]);
+        cnt = 0u;
+    }
+    __syncthreads();
+    const double dt = sdt[0], t = sdt[1];
+    if (a.final_stage && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;
+        a.clk->rate[s2] = 0ull;
+        if (!(dt > 0.0)) {
+            a.clk->t[s1] = t;
+            a.clk->rate[s1] = a.clk->rate[a.slot];
+        } else {
+            a.clk->t[s1] = t + dt;
+            a.clk->last_dt = dt;
+            if (a.dt_hist && a.clk->steps < a.dt_hist_cap) a.dt_hist[a.clk->steps] = dt;
+            a.clk->steps += 1;
+        }
+    }
+    if (!(dt > 0.0)) return;
+
+    const Grid2D& g = a.g;
+    const int i0 = blockIdx.x * G::TX, j0 = blockIdx.y * G::TY;
+    // final stage: the owned cells' U^n and W^n are needed only after the
+    // face fluxes; start moving them into L2 now
+    if (a.final_stage) {
+        for (int c = tid; c < G::NC; c += NTP) {
+            const int gi = i0 + c % G::TX, gj = j0 + c / G::TX;
+            if (gi < g.nx && gj < g.ny) {
+                const long long o = (long long)gj * g.pitch + gi;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Ubase + o + PH::ufield(k) * g.fstride));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Wbase + o + k * g.fstride));
+                }
+            }
+        }
+    }
+    const bool interior = i0 >= 2 && j0 >= 2 && i0 + G::TX + 2 <= g.nx && j0 + G::TY + 2 <= g.ny;
+    if (interior) {      // the whole box inside the grid: asynchronous copies, no ghost cells
+        const float* src = a.Win + (long long)(j0 - 2) * g.pitch + (i0 - 2);
+        for (int c = tid; c < G::NBOX; c += NTP) {
+            const float* s0 = src + (long long)(c / G::BX) * g.pitch + c % G::BX;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) cp_async4(W + k * G::NBOX + c, s0 + k * g.fstride);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    } else {
+        for (int c = tid; c < G::NBOX; c += NTP) {
+            const int bx = c % G::BX, by = c / G::BX;
+            float Q[NF];
+            load_prim_f32<PH>(a, i0 + bx - 2, j0 + by - 2, Q);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) W[k * G::NBOX + c] = Q[k];
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();
+    for (int n = tid; n < G::NLIM; n += NTP) {
+        if (n < G::NC) {                   // owned cell: both directions
+            const int bx = 2 + n % G::TX, by = 2 + n / G::TX;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (p.order == 2) v = phi_pair_m<NF, G::NBOX, G::BX>(W, by * G::BX + bx, p.limiter);
+            phx[(by - 2) * (G::TX + 2) + bx - 1] = v.x;
+            phy[(by - 1) * G::TX + bx - 2] = v.y;
+        } else if (n < G::NC + 2 * G::TY) {     // halo column: x only
+            const int m = n - G::NC;
+            const int bx = (m < G::TY) ? 1 : G::TX + 2, by = 2 + m % G::TY;
+            float v = 0.0f;
+            if (p.order == 2) v = phi_one_m<NF, G::NBOX>(W, by * G::BX + bx, 1, p.limiter);
+            phx[(by - 2) * (G::TX + 2) + bx - 1] = v;
+        } else {                                // halo row: y only
+            const int m = n - G::NC - 2 * G::TY;
+            const int by = (m < G::TX) ? 1 : G::TY + 2, bx = 2 + m % G::TX;
+            float v = 0.0f;
+            if (p.order == 2) v = phi_one_m<NF, G::NBOX>(W, by * G::BX + bx, G::BX, p.limiter);
+            phy[(by - 1) * G::TX + bx - 2] = v;
+        }
+    }
+    __syncthreads();
+
+    const double sl64 = a.sp.sigma_lim, kw64 = a.sp.k_ws;
+    unsigned nflag = 0;
+#pragma unroll 1
+    for (int f = tid; f < G::NFX; f += NTP) {       // x faces: TY rows of TX + 1
+        const int fx = f % (G::TX + 1), fy = f / (G::TX + 1);
+        float F[NF];
+        face_flux_x2<0, G::NBOX>(W, (fy + 2) * G::BX + fx + 1, 1, phx[fy * (G::TX + 2) + fx],
+                                 phx[fy * (G::TX + 2) + fx + 1], p, mp, sl64, kw64, F, nflag);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Fx[k * G::NFX + f] = F[k];
+    }
+#pragma unroll 1
+    for (int f = tid; f < G::NFY; f += NTP) {       // y faces: TY + 1 rows of TX
+        const int fx = f % G::TX, fy = f / G::TX;
+        float F[NF];
+        face_flux_x2<1, G::NBOX>(W, (fy + 1) * G::BX + fx + 2, G::BX, phy[fy * G::TX + fx],
+                                 phy[(fy + 1) * G::TX + fx], p, mp, sl64, kw64, F, nflag);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Fy[k * G::NFY + f] = F[k];
+    }
+    __syncthreads();
+
+    float r = 0.0f;
+    const float cdt = scdt;
+    const bool implicit = p.tau_model != 0 && p.src_implicit;
+#pragma unroll 1
+    for (int c = tid; c < G::NC; c += NTP) {
+        const int cx = c % G::TX, cy = c / G::TX;
+        const int gi = i0 + cx, gj = j0 + cy;
+        if (gi >= g.nx || gj >= g.ny) continue;
+        const long long o = (long long)gj * g.pitch + gi;
+        const int cb = (cy + 2) * G::BX + cx + 2;
+        // final stage: this cell's W^n and U^n, loaded first so that their
+        // latency overlaps the source and flux-difference arithmetic
+        float Wc[NF];
+        double Ub[NF];
+        if (a.final_stage) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                Wc[k] = a.Wbase[o + k * g.fstride];
+                Ub[k] = a.Ubase[o + PH::ufield(k) * g.fstride];
+            }
+        }
+        float L[NF], Qc[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Qc[k] = W[k * G::NBOX + cb];
+        if (p.tau_model != 0 && !p.src_implicit) {
+            PH::source(Qc, PH::tau(p, Qc), L);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) L[k] = 0.0f;
+        }
+        const int ex = cy * (G::TX + 1) + cx, ey = cy * G::TX + cx;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            L[k] -= (Fx[k * G::NFX + ex + 1] - Fx[k * G::NFX + ex]) * a.idxf;
+            L[k] -= (Fy[k * G::NFY + ey + G::TX] - Fy[k * G::NFY + ey]) * a.idyf;
+        }
+        float dU[NF], Wn[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dU[k] = cdt * L[k];
+        if (!a.final_stage) {
+            // W* = prim(U^n + dt/2 L): the base primitives are this cell's W^n (= stencil)
+            PH::increment(Qc, dU, Wn);
+            if (implicit) {      // point-implicit source over cdt
+                float N[NF];
+                PH::relax_prim(Wn, 1.0f / (1.0f + cdt / PH::tau(p, Wn)), N);
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) a.Wout[o + k * g.fstride] = Wn[k];
+        } else {
+            PH::increment(Wc, dU, Wn);
+            if (implicit) {      // relax W, and U by (g - 1)(U - U_M)
+                float N[NF];
+                float gm = 1.0f / (1.0f + cdt / PH::tau(p, Wn));
+                PH::relax_prim(Wn, gm, N);
+#pragma unroll
+                for (int k = 0; k < NF; ++k) dU[k] += (gm - 1.0f) * N[k];
+            }
+            // U^{n+1} = U^n + dU in FP64 (the conservation accumulator);
+            // a non-finite increment marks the state non-finite
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                a.Uout[o + PH::ufield(k) * g.fstride] = Ub[k] + f32_to_f64_bits(dU[k]);
+                bad |= !(fabsf(dU[k]) < __int_as_float(0x7f800000));
+            }
+            if (a.resync) {      // the periodic re-sync: W^{n+1} = prim(U^{n+1}) in FP64
+                double Un[NF], Q64[NF];
+#pragma unroll
+                for (int k = 0; k < NF; ++k) Un[k] = a.Uout[o + PH::ufield(k) * g.fstride];
+                PH::cons2prim_fast(Un, Q64);
+#pragma unroll
+                for (int k = 0; k < NF; ++k) Wn[k] = (float)Q64[k];
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) a.Wout[o + k * g.fstride] = Wn[k];
+            if (PH::nonpositive(Wn)) atomicOr(&a.clk->status, ST_NONPOSITIVE);
+            if (bad) atomicOr(&a.clk->status, ST_NONFINITE);
+            float ax, ay;
+            x2::rates_x2(Wn, p.sigma_lim, p.k_ws, ax, ay);
+            float rc = ax * a.idxf + ay * a.idyf;
+            if (!(rc >= 0.0f)) rc = __int_as_float(0x7f800000);     // NaN -> inf
+            r = fmaxf(r, rc);
+        }
+    }
+    unsigned wf = __reduce_add_sync(0xffffffffu, nflag);
+    if ((tid & 31) == 0 && wf) atomicAdd(&cnt, wf);
+    if (a.final_stage) block_max_atomic_m(r, &a.clk->rate[(a.slot + 1) % 3], red);
+    __syncthreads();
+    if (tid == 0) {
+        atomicAdd(&a.clk->n_face, (unsigned long long)(2 * (G::NFX + G::NFY)));
+        if (cnt) atomicAdd(&a.clk->n_face64, (unsigned long long)cnt);
+    }
+}
+
+// planar state, packed face-state pairs, 15 x 32 tile, three blocks per SM
+extern "C" __global__ void __launch_bounds__(NTP, 3)
 mxe_stage14_2d_mixed_planar_x2(const Stage2DArgs a, const ParamsT<float> p,
                                const MixedPolicy mp) {
-    stage_mixed<PhysPlanar, false, true>(a, p, mp);
+    stage_mixed_x2<TileP>(a, p, mp);
 }
+size_t stage14_2d_mixed_x2_smem() { return smem_mixed_x2<TileP>(); }
+int stage14_2d_mixed_x2_tile_x() { return TileP::TX; }
+int stage14_2d_mixed_x2_tile_y() { return TileP::TY; }
 
 size_t stage14_2d_mixed_smem(bool planar, int blocks_per_sm) {
     if (!planar) return smem_mixed<14, false>();      // both general variants

@@ -57,8 +57,8 @@ __device__ __forceinline__ v2 sigma_root_x2(v2 A, v2 X, v2 T2) {
     v2 fT = mul(T2, S(4.0f));
     v2 s1 = add(A, rt);                // A >= 0
     v2 dn = mul(fT, sub(rt, A));       // A < 0
-    return make_float2(A.x >= 0.0f ? __fdividef(s1.x, fT.x) : __fdividef(X.x, dn.x),
-                       A.y >= 0.0f ? __fdividef(s1.y, fT.y) : __fdividef(X.y, dn.y));
+    return div_(make_float2(A.x >= 0.0f ? s1.x : X.x, A.y >= 0.0f ? s1.y : X.y),
+                make_float2(A.x >= 0.0f ? fT.x : dn.x, A.y >= 0.0f ? fT.y : dn.y));
 }
 
 __device__ __forceinline__ void dimless_x2(const v2* Q, DimX2& g) {
@@ -208,13 +208,10 @@ __device__ __forceinline__ v2 hyp_x2(v2 z, v2 D0) {
     return make_float2(hyp1(z.x, D0.x, D.x, rt.x), hyp1(z.y, D0.y, D.y, rt.y));
 }
 
-// Eq. (14mom-approx-ws-equations) along K with q_perp = |q*_O|: the
-// dimensionless lambda*_max (lp) and lambda*_min (lm).
-template <int K>
-__device__ __forceinline__ void lam_x2(const DimX2& g, v2 sb, v2 isb, v2 ssb, v2& lp, v2& lm) {
-    const v2 Pkk = K == 0 ? g.a : g.d;
-    const v2 qd = K == 0 ? g.qx : g.qy;
-    const v2 qperp = abs_(K == 0 ? g.qy : g.qx);
+// Eq. (14mom-approx-ws-equations) for two (P*_kk, q*_k, |q*_perp|) triples
+// at once: the dimensionless lambda*_max (lp) and lambda*_min (lm).
+__device__ __forceinline__ void lam_core_x2(v2 Pkk, v2 qd, v2 qperp, v2 sb, v2 isb, v2 ssb,
+                                            v2& lp, v2& lm) {
     v2 l2 = lg2(Pkk);
     v2 Pkk2 = mul(Pkk, Pkk);
     v2 a = mul(ex2(fma(Pkk2, S(-LOG2E), mul(l2, S(1.1f)))), S(1.4f));
@@ -235,6 +232,30 @@ __device__ __forceinline__ void lam_x2(const DimX2& g, v2 sb, v2 isb, v2 ssb, v2
     lm = neg(fma(pre, hyp_x2(zm, fma(zm, m08, base)), E));
 }
 
+// The same along K for two face states, q_perp = |q*_O|.
+template <int K>
+__device__ __forceinline__ void lam_x2(const DimX2& g, v2 sb, v2 isb, v2 ssb, v2& lp, v2& lm) {
+    lam_core_x2(K == 0 ? g.a : g.d, K == 0 ? g.qx : g.qy, abs_(K == 0 ? g.qy : g.qx), sb, isb,
+                ssb, lp, lm);
+}
+
+// CFL rates max(|lambda_min|, |lambda_max|) of one cell state in x and y
+// (the two directions as the lanes of one wave-speed evaluation).
+__device__ __forceinline__ void rates_x2(const float* Q, float sigma_lim, float k_ws, float& ax,
+                                         float& ay) {
+    DimlessP<float> g;
+    dimless_p(Q, g);
+    const float sb = clamp_sigma(g.sig, sigma_lim);
+    v2 lp, lm;
+    lam_core_x2(make_float2(g.a, g.d), make_float2(g.qx, g.qy),
+                make_float2(fabsf(g.qy), fabsf(g.qx)), S(sb), S(1.0f / sb), S(sqrtf(sb)), lp, lm);
+    const v2 u = make_float2(Q[1], Q[2]);
+    const v2 ks = S(k_ws * g.sq);
+    const v2 hi = fma(lp, ks, u), lo = fma(lm, ks, u);
+    ax = fmaxf(fabsf(lo.x), fabsf(hi.x));
+    ay = fmaxf(fabsf(lo.y), fabsf(hi.y));
+}
+
 // Both face states of a face: conserved U, K-flux F, wave speeds, and the
 // raw sigma and det P* (the conditioning the mixed policy checks).
 template <int K>
@@ -243,7 +264,8 @@ __device__ __forceinline__ void face_eval_x2(const v2* Q, float sigma_lim, float
     DimX2 g;
     dimless_x2(Q, g);
     v2 sb = clamp_sigma_x2(g.sig, sigma_lim);
-    v2 isb = rcp(sb), ssb = sqrt_(sb);
+    v2 rsb = rsqrt_(sb);
+    v2 isb = mul(rsb, rsb), ssb = mul(sb, rsb);       // 1/sigma, sqrt(sigma)
     v2 QK[4], RK[2], SK;
     closure_x2<K>(g, sb, isb, ssb, QK, RK, SK);
     v2 u2, Pux, Puy;
