@@ -622,12 +622,15 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
 
 // ---------------------------------------------------------------------------
 // Packed planar stage (the default for planar states).  A block of NTP
-// threads owns a TX x TY tile; every thread evaluates two x faces and two y
-// faces as packed pairs of face states, the limiters of about two cells
-// (both directions of an interior cell in one evaluation), and updates two
-// cells.  The taller tile halves the halo cells loaded, the limiters
-// evaluated and the faces computed twice per owned cell, and the per-block
-// fixed work, against the 15 x 16 tile of the scalar kernels.
+// threads owns a TX x TY tile; every thread evaluates up to two x faces and
+// two y faces as packed pairs of face states, the limiters of about two
+// cells (both directions of an interior cell in one evaluation), and
+// updates up to two cells.  The tile is 31 x 15: a row of 32 x faces is one
+// warp (no shared-memory bank conflicts in the face phase), the owned cells
+// of a warp sit in one or two rows (124-byte segments of each field in
+// global memory), and against the 15 x 16 tile of the scalar kernels the
+// halo cells loaded, the limiters evaluated and the faces computed twice
+// per owned cell, and the per-block fixed work, are about halved.
 template <int TX_, int TY_>
 struct TileGeo {
     static constexpr int TX = TX_, TY = TY_;
@@ -641,7 +644,7 @@ struct TileGeo {
     // columns (x only) and the halo rows (y only)
     static constexpr int NLIM = NC + 2 * TY + 2 * TX;
 };
-using TileP = TileGeo<15, 32>;
+using TileP = TileGeo<31, 15>;
 constexpr int NTP = 256;
 static_assert(TileP::NFX <= 2 * NTP && TileP::NFY <= 2 * NTP && TileP::NC <= 2 * NTP,
               "two faces per direction and two cells per thread");
