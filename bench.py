@@ -30,28 +30,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s 14-mom 2D RK2 (% HBM roofline), mixed vs FP64; adjoint/fwd ratio"
 UNIT = "cell-updates/s"
-# algorithmic bytes per cell-update (each stage reads its inputs once and
-# writes its output once):
+# Algorithmic bytes per cell-update (one cell advanced one full RK2 step):
+# each stage reads its inputs once and writes its output once, 14 fields.
 #   fp64 : stage 1 reads U^n, writes U*; stage 2 reads U*, U^n, writes
 #          U^{n+1}: 5 x 14 x 8 B = 560 B
-#   mixed: stage 1 reads W^n (FP32 primitives), writes W* (FP32); stage 2
-#          reads W*, U^n (FP64), W^n, writes U^{n+1} (FP64), W^{n+1}:
-#          (2 + 3) x 56 B + 2 x 112 B = 504 B
-#   planar states (u_z, P_xz, P_yz, q_z identically zero, as in the crossed
-#   jets): ten fields instead of fourteen -> fp64 400 B, mixed 360 B
-BYTES_PER_CELL_UPDATE = {("fp64", False): 560.0, ("mixed", False): 504.0,
-                         ("fp64", True): 400.0, ("mixed", True): 360.0}
+#   mixed: U^n FP64 (the conservation accumulator), U* FP32: stage 1 reads
+#          U^n (112), writes U* (56); stage 2 reads U* (56), U^n (112),
+#          writes U^{n+1} (112): 448 B
+# This is the roofline's basis.  The kernels move less for planar states
+# (u_z, P_xz, P_yz, q_z identically zero, as in the crossed jets): ten
+# fields, and the mixed path carries FP32 primitives W beside U^n:
+#   fp64 planar 400 B; mixed planar: stage 1 reads W, writes Ws (2 x 40);
+#   stage 2 reads Ws, U^n, W, writes U^{n+1}, W (3 x 40 + 2 x 80): 360 B
+BYTES_PER_CELL_UPDATE = {"fp64": 560.0, "mixed": 448.0}
+PLANAR_BYTES_PER_CELL_UPDATE = {"fp64": 400.0, "mixed": 360.0}
 # DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the two stage launches of one step, 2048^2
 # crossed jets, 4.19e6 cells; scaled to the benchmark grid by cell count)
-TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 340.5}
-# Issue-rate roofline of the mixed planar stage kernel (it is bound by
-# instruction issue, not by DRAM): thread instructions per cell-update over
-# both stages (ncu smsp__inst_executed.sum x 32 / cells, 1024^2 crossed
-# jets) against 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
-THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 7094.5}
-KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed",
-          ("fp64", True): "mxe_stage14_2d_f64_planar", ("mixed", True): "mxe_stage14_2d_mixed_planar_b3"}
+TRAFFIC_PER_CELL_UPDATE = {("mixed", True): None}
+# Issue-rate roofline of the mixed planar stage kernel (bound by instruction
+# issue, not by DRAM): thread instructions per cell-update over both stages
+# (ncu smsp__inst_executed.sum x 32 / cells, 2048^2 crossed jets) against
+# 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
+THREAD_INST_PER_CELL_UPDATE = {("mixed", True): None}
+KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed_b3",
+          ("fp64", True): "mxe_stage14_2d_f64_planar",
+          ("mixed", True): "mxe_stage14_2d_mixed_planar_x2"}
 
 
 def parse():
@@ -59,6 +63,8 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--prerun", type=int, default=1000,
+                   help="untimed steps from the developed state before warm-up and timing")
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--compare-steps", type=int, default=10,
@@ -74,7 +80,13 @@ def parse():
                    help="skip the adjoint leg (512^2 crossed jets, 500 steps, checkpoints every 50)")
     p.add_argument("--no-jet", action="store_true",
                    help="skip the single collisionless jet leg (1200^2, forward Euler)")
-    p.add_argument("--only", default=None, choices=["batch", "adjoint"],
+    p.add_argument("--no-l1", action="store_true",
+                   help="skip the per-field mixed-vs-FP64 L1 leg (1024^2, 200 steps)")
+    p.add_argument("--no-dt-history", action="store_true",
+                   help="skip the crossing collisionless jets step-size history (1200^2, 10000 steps)")
+    p.add_argument("--cpu-full", action="store_true",
+                   help="CPU baseline: also config 2 to t = 0.2 and config 3 at 1024^2 for 20 steps")
+    p.add_argument("--only", default=None, choices=["batch", "adjoint", "cpu", "l1", "dt"],
                    help="run one secondary leg alone (profiling runs)")
     p.add_argument("--batch-t-end", type=float, default=0.2)
     p.add_argument("--adj-n", type=int, default=512)
@@ -241,31 +253,236 @@ def make_solver(mx, wl, n, precision, setup):
     return s
 
 
-def cpu_baseline(wl, seconds_target=15.0):
-    """The FP64 oracle as it stands (single thread) on a bounded sample of the
-    same workload: a 128 x 128 crossed-jets grid of the same set-up."""
+def cpu_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
+def _jets_oracle(oracle, wl, n):
+    """The crossed-jets workload on an n x n grid for the oracle: its
+    configuration and the developed state (conserved, (n, n, 14))."""
     import numpy as np
-    import oracle
-    n = 128
     setup = wl.jets_setup(Kn=0.1)
     prim = wl.jets_like_field(n, n, setup)
-    U = np.array([oracle.prim2cons(q) for q in prim.reshape(-1, 14)]).reshape(n, n, 14)
+    U = oracle.prim2cons_field(prim)
     lo, hi = setup["slot"]
     sides = [{"type": 0, "spans": [(lo, hi, setup["left"])]}, {"type": 0},
              {"type": 0, "spans": [(lo, hi, setup["bottom"])]}, {"type": 0}]
     cfg = oracle.make_cfg(system=14, nx=n, ny=n, tau_model=2, tau_ref=setup["tau_ref"],
                           rho_ref=setup["rho_ref"], T_ref=setup["T_ref"], sides=sides)
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        dt = oracle.dt(cfg, U, 0.0, 10.0)
-        U = oracle.step(cfg, U, dt)
+    return cfg, np.ascontiguousarray(U)
+
+
+def _timed_steps(oracle, cfg, U, omp, seconds, max_steps):
+    """RK2 steps of the oracle (CFL step included) until `seconds` or
+    `max_steps`; returns (steps, elapsed seconds)."""
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0, omp=omp), omp=omp)
         steps += 1
-        el = time.perf_counter() - t0
-        if el > seconds_target or steps >= 50:
+        if time.perf_counter() - t0 > seconds:
             break
-    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n}x{n} crossed jets, {steps} RK2 steps incl. CFL, {el:.1f} s, 1 thread"}
+    return steps, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, full=False):
+    """The FP64 oracle as it stands on the host cores: single-threaded (the
+    paper's 1-core basis) and its OpenMP build on all cores (bitwise the
+    same arithmetic), on bounded samples of the benchmark configurations:
+    config 3 (crossed jets, RK2, MUSCL, HLL) on a 128^2 grid, config 1
+    (5-moment Sod, 1000 cells, first order, forward Euler) to t = 0.2 in full,
+    config 2 (14-moment Sod, 4096 cells, RK2, Kn = 0.01) over its first 100
+    steps.  full: also config 2 to t = 0.2 and config 3 at 1024^2 for 20
+    steps (minutes of CPU time).  Rate = cell-updates/s."""
+    import oracle
+    oracle.build()
+    oracle.build(omp=True)
+    info = cpu_info()
+    threads = oracle.threads(omp=True)
+    out = {"kind": "oracle", "unit": UNIT, **info, "threads_all_core": threads}
+
+    def leg(name, cells, run):
+        r = {}
+        for omp in (False, True):
+            n, el = run(omp)
+            r["all_core" if omp else "single_thread"] = {
+                "value": cells * n / el, "steps": n, "seconds": el,
+                "threads": threads if omp else 1}
+        r["cells"] = cells
+        out[name] = r
+
+    def c3(n, seconds, max_steps):
+        def run(omp):
+            cfg, U = _jets_oracle(oracle, wl, n)
+            return _timed_steps(oracle, cfg, U, omp, seconds, max_steps)
+        return run
+
+    def sod(system, nx, order, integ, t_end, max_steps):
+        import numpy as np
+
+        def run(omp):
+            U = oracle.prim2cons_field(wl.sod_prim(system, nx)[None])
+            cfg = oracle.make_cfg(system=system, nx=nx, ny=1, order=order, integrator=integ,
+                                  tau_model=oracle.TAU_HARDSPHERE, tau_ref=wl.sod_tau_ref(0.01))
+            t0 = time.perf_counter()
+            _, _, hist = oracle.run(cfg, np.ascontiguousarray(U), 0.0, t_end, max_steps, omp=omp)
+            return len(hist), time.perf_counter() - t0
+        return run
+
+    leg("config3_jets_128", 128 * 128, c3(128, 8.0, 200))
+    leg("config1_sod5_1000_to_t0.2", 1000, sod(5, 1000, 1, oracle.FE, 0.2, 10 ** 6))
+    leg("config2_sod14_4096_100_steps", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 100))
+    if full:
+        leg("config2_sod14_4096_to_t0.2", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 10 ** 7))
+        leg("config3_jets_1024_20_steps", 1024 * 1024, c3(1024, 1e9, 20))
+    h = out["config3_jets_128"]["all_core"]
+    out["value"] = h["value"]
+    out["cores"] = threads
+    out["sample"] = (f"128x128 crossed jets (the benchmark workload's set-up), {h['steps']} RK2 "
+                     f"steps incl. CFL, {h['seconds']:.1f} s, OpenMP build on {threads} threads; "
+                     f"single-thread and configs 1-2 beside it")
+    return out
+
+
+def bench_mixed_l1(mx, wl, stream, n=1024, steps=200):
+    """Per-field error of the mixed path against the all-FP64 GPU path
+    (held to 1e-12 of the FP64 oracle by the parity tests), crossed jets from
+    the developed state, same step sizes.  Bound (fixed before measuring):
+    10x the relative L1 change of the FP64 path when every primitive of the
+    initial and inflow states is perturbed by 1e-7 relative (the data
+    resolution of FP32).  Fields: the 14 conserved moments (the gate of the
+    tests), and the primitive density, velocity, temperature, heat flux."""
+    import numpy as np
+    setup = wl.jets_setup(Kn=0.1)
+    rng = np.random.default_rng(n)
+    prim = np.ascontiguousarray(np.moveaxis(wl.jets_like_field(n, n, setup), -1, 0))
+
+    def run(precision, st, init, dts=None):
+        s = make_solver(mx, wl, n, precision, st)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(init)
+        if dts is None:
+            s.set_dt_history(steps)
+            s.step(steps, float("inf"))
+            dts = s.dt_history(steps)
+        else:
+            s.step_dt(dts)
+        return s.get_moments("conserved"), s.get_moments("primitive"), dts
+
+    A, Ap, dts = run("fp64", setup, prim)
+    pert = lambda x: x * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=np.shape(x)))
+    a = math.sqrt(wl.GAMMA_3D)
+    r1, u1, T1 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    r2, u2, T2 = pert(np.array([1.0, 3.0 * a, 1.0]))
+    setup_p = dict(setup, left=wl.maxwellian14(r1, u1, 0.0, T1),
+                   bottom=wl.maxwellian14(r2, 0.0, u2, T2))
+    B, Bp, _ = run("fp64", setup_p, pert(prim), dts)
+    G, Gp, _ = run("mixed", setup, prim, dts)
+
+    def l1(a, b):
+        a = a.reshape(a.shape[0], -1); b = b.reshape(b.shape[0], -1)
+        den = np.abs(b).sum(1)
+        return np.abs(a - b).sum(1) / np.where(den > 0, den, 1.0)
+
+    names = ["rho", "rho_ux", "rho_uy", "rho_uz", "Exx", "Exy", "Exz", "Eyy", "Eyz", "Ezz",
+             "Hx", "Hy", "Hz", "E4"]
+    e, sens = l1(G, A), l1(B, A)
+    nz = np.abs(A).reshape(14, -1).sum(1) > 0
+    bound = np.maximum(10 * sens, 1e-10)
+
+    def derived(P):            # rho, u_x, u_y, T, q_x, q_y, R/(rho theta^2)
+        rho = P[0]
+        T = (P[4] + P[7] + P[9]) / (3 * rho)
+        return np.stack([rho, P[1], P[2], T, P[10], P[11], P[13] / (rho * T * T)])
+
+    dn = ["rho", "u_x", "u_y", "T", "q_x", "q_y", "R_star"]
+    ed, sd = l1(derived(Gp), derived(Ap)), l1(derived(Bp), derived(Ap))
+    return {
+        "workload": f"crossed jets {n}x{n} from the developed state, {steps} RK2 steps "
+                    f"(t = {float(dts.sum()):.3e}), mixed vs all-FP64 GPU path, same step sizes",
+        "conserved": {nm: {"l1": float(e[k]), "bound": float(bound[k])}
+                      for k, nm in enumerate(names) if nz[k]},
+        "primitive": {nm: {"l1": float(ed[k]), "bound": float(max(10 * sd[k], 1e-10))}
+                      for k, nm in enumerate(dn)},
+        "max_l1_over_bound": float((e[nz] / bound[nz]).max()),
+        "within_bound": bool(np.all(e[nz] <= bound[nz])),
+    }
+
+
+def bench_dt_history(mx, wl, stream, n=1200, steps=10000):
+    """Sec. 6 crossing collisionless jets (Mach 5, width L/7, background 1e-5
+    of the jet density, no collision source), 1200^2, MUSCL + forward Euler
+    at CFL 0.5, mixed precision: the step-size history over `steps` steps
+    (the paper reports the step size collapsing near step 9000 on its
+    1200^2 grid).  Reports the step size at chosen steps, its minimum, and
+    the first step whose size falls below a tenth (and a hundredth) of the
+    size at step 100."""
+    import numpy as np
+    import torch
+    setup = wl.collisionless_jets_setup(2)
+    lo, hi = setup["slot"]
+    bg = setup["background"]
+    s = mx.Solver(system=14, nx=n, ny=n, precision="mixed", order=2, integrator="fe",
+                  flux="hll", limiter="minmod", cfl=0.5, sigma_lim=1e-4)
+    s.set_stream(stream.cuda_stream)
+    for side in (mx.XLO, mx.XHI, mx.YLO, mx.YHI):
+        s.set_bc(side, mx.BC_DIRICHLET, 0.0, 0.0, bg)
+    s.set_bc(mx.XLO, mx.BC_DIRICHLET, lo, hi, setup["left"])
+    s.set_bc(mx.YLO, mx.BC_DIRICHLET, lo, hi, setup["bottom"])
+    s.set_state(np.ascontiguousarray(np.moveaxis(wl.jets_initial(n, n, setup), -1, 0)))
+    s.set_dt_history(steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stop = None
+    try:                       # stops early if the step size collapses to zero
+        s.step(steps, float("inf"))
+    except mx.MaxentError as e:
+        stop = str(e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    d = s.diagnostics()
+    taken = int(d["steps"])
+    dts = s.dt_history(taken)
+    ref = float(dts[100]) if taken > 100 else float(dts[0])
+
+    def first_below(f):
+        k = np.nonzero(dts < f * ref)[0]
+        return int(k[0]) if k.size else None
+
+    marks = [k for k in (0, 100, 1000, 2000, 3000, 4000, 5000, 6000, 7000, 8000, 9000, 10000)
+             if k < taken] + [taken - 1]
+    return {"workload": f"two crossing collisionless jets {n}x{n}, Mach 5, FE MUSCL HLL minmod, "
+                        f"CFL 0.5, mixed, up to {steps} steps",
+            "steps_taken": taken, "stopped": stop,
+            "dt_at_step": {str(k): float(dts[k]) for k in marks}, "dt_min": float(dts.min()),
+            "step_of_dt_min": int(np.argmin(dts)), "t_final": float(dts.sum()),
+            "first_step_dt_below_0.1_of_step100": first_below(0.1),
+            "first_step_dt_below_0.01_of_step100": first_below(0.01),
+            "ms_per_step": ms / max(taken, 1), "n_nonfinite": d["n_nonfinite"],
+            "n_nonpositive": d["n_nonpositive"], "n_sigma_above_one": d["n_sigma_above_one"],
+            "n_sigma_below_lim": d["n_sigma_below_lim"],
+            "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"])
+            if d["n_closures"] else None}
 
 
 def bench_batch(mx, wl, stream, world, t_end=0.2):
@@ -429,44 +646,46 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
     return out
 
 
-def workload_config(n, precision, world, planar=True):
+def workload_config(n, precision, world, planar=True, prerun=0):
     """The benchmark's workload, as named in both arms' JSON lines."""
     return {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
             "n": n, "precision": precision, "flux": "hll", "limiter": "minmod",
             "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
+            "initial": f"background at rest, jets from the slots; timed after {prerun} untimed steps",
             "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"}
 
 
 def run_reference(args, wl):
+    """The reference arm: the FP64 oracle on the host cores (its OpenMP
+    build, bitwise the arithmetic of the single-threaded oracle), each step
+    one RK2 step (CFL included) of a bounded 96^2 sample of the crossed-jets
+    workload, rank 0 only."""
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
         return
-    import numpy as np
     import oracle
+    oracle.build(omp=True)
+    threads = oracle.threads(omp=True)
     n = 96
-    setup = wl.jets_setup(Kn=0.1)
-    prim = wl.jets_like_field(n, n, setup)
-    U = np.array([oracle.prim2cons(q) for q in prim.reshape(-1, 14)]).reshape(n, n, 14)
-    lo, hi = setup["slot"]
-    sides = [{"type": 0, "spans": [(lo, hi, setup["left"])]}, {"type": 0},
-             {"type": 0, "spans": [(lo, hi, setup["bottom"])]}, {"type": 0}]
-    cfg = oracle.make_cfg(system=14, nx=n, ny=n, tau_model=2, tau_ref=setup["tau_ref"],
-                          rho_ref=setup["rho_ref"], T_ref=setup["T_ref"], sides=sides)
+    cfg, U = _jets_oracle(oracle, wl, n)
     for _ in range(args.warmup):
-        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0))
+        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0, omp=True), omp=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0))
+        U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0, omp=True), omp=True)
     el = time.perf_counter() - t0
     v = n * n * args.steps / el
-    sample = f"{n}x{n} crossed jets per step (bounded sample of the {args.n}^2 workload), 1 thread"
+    info = cpu_info()
+    sample = (f"{n}x{n} crossed jets per step (bounded sample of the {args.n}^2 workload), "
+              f"OpenMP oracle on {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": workload_config(args.n, "fp64 (oracle)", args.gpus),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample, **info},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -477,6 +696,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, wl)
         return
+    if args.only == "cpu":              # host cores only
+        print(json.dumps(finite_json({"only": "cpu", "cpu": cpu_baseline(wl, args.cpu_full)})),
+              flush=True)
+        return
     import numpy as np
     import torch
     world, rank, local, dist = dist_setup(args)
@@ -486,6 +709,12 @@ def main():
         stream = torch.cuda.Stream()
         if args.only == "batch":
             leg = bench_batch(mx, wl, stream, world, args.batch_t_end)
+        elif args.only == "cpu":
+            leg = cpu_baseline(wl, args.cpu_full)
+        elif args.only == "l1":
+            leg = bench_mixed_l1(mx, wl, stream)
+        elif args.only == "dt":
+            leg = bench_dt_history(mx, wl, stream)
         else:
             leg = bench_adjoint(world, args.adj_n, args.adj_steps, args.adj_ckpt,
                                 args.adj_precision)
@@ -495,7 +724,12 @@ def main():
 
     n = args.n
     setup = wl.jets_setup(Kn=0.1)
-    prim = np.ascontiguousarray(np.moveaxis(wl.jets_like_field(n, n, setup), -1, 0))
+    # the run of config 3: background at rest, jets entering through the slots
+    # (the timed steps follow args.prerun untimed ones); the synthetic
+    # developed state (a filled domain) is timed beside it
+    rest = np.ascontiguousarray(np.moveaxis(wl.jets_initial(n, n, setup), -1, 0))
+    developed = np.ascontiguousarray(np.moveaxis(wl.jets_like_field(n, n, setup), -1, 0))
+    prim = rest
     ncell = n * n
     stream = torch.cuda.Stream()
 
@@ -504,15 +738,18 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def timed(precision, steps, sample_clocks):
+    def timed(precision, steps, sample_clocks, prerun=0, init=None):
         s = make_solver(mx, wl, n, precision, setup)
         s.set_stream(stream.cuda_stream)
         if precision == "mixed" and args.scalar_faces:
             s.set_face_packing(False)
-        s.set_state(prim)
+        s.set_state(prim if init is None else init)
+        if prerun:                  # untimed steps of the run first
+            s.step(prerun, float("inf"))
         for _ in range(args.warmup):
             s.step(1, float("inf"), sync=False)
         barrier()
+        s.diag0 = s.diagnostics()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         sampler = ClockSampler(local) if sample_clocks else None
         if sampler:
@@ -531,12 +768,34 @@ def main():
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
         total_ms = max_over_ranks(total_ms, dist)
+        # every timed step must have advanced the solution: a step whose
+        # CFL size collapsed to zero does no work and would inflate the rate
+        d1 = s.diagnostics()
+        if d1["steps"] - s.diag0["steps"] != steps or d1["n_nonpositive"] or d1["n_nonfinite"]:
+            raise RuntimeError(f"timed {precision} steps did not all advance: "
+                               f"{d1['steps'] - s.diag0['steps']} of {steps}, "
+                               f"non-positive cells {d1['n_nonpositive']}, "
+                               f"non-finite {d1['n_nonfinite']}")
         return s, per, total_ms, sampler
 
-    s, per, total_ms, clk = timed(args.precision, args.steps, True)
+    s, per, total_ms, clk = timed(args.precision, args.steps, True, args.prerun)
     d = s.diagnostics()
+    d0 = s.diag0
     planar = bool(d["planar"])
+    n_cl = d["n_closures"] - d0["n_closures"]
+    fp64_share = (d["n_fp64_closures"] - d0["n_fp64_closures"]) / n_cl if n_cl else None
     value = whole_job_value(ncell * args.steps, world, total_ms)
+    # the same kernels on the synthetic developed state (every cell in the
+    # jets' non-equilibrium mix), first steps, no pre-run
+    dsteps = max(10, min(args.steps, 20))
+    sd, perd, totd, _ = timed(args.precision, dsteps, False, 0, developed)
+    dd1, dd0 = sd.diagnostics(), sd.diag0
+    ncd = dd1["n_closures"] - dd0["n_closures"]
+    developed_leg = {"value": whole_job_value(ncell * dsteps, world, totd), "unit": UNIT,
+                     "steps": dsteps, "ms_per_step": totd / dsteps,
+                     "fp64_closure_share": ((dd1["n_fp64_closures"] - dd0["n_fp64_closures"]) / ncd
+                                            if ncd else None)}
+    del sd
     other = "fp64" if args.precision == "mixed" else "mixed"
     csteps = args.compare_steps or args.steps
     s2, per2, total2, _ = timed(other, csteps, False)
@@ -545,17 +804,20 @@ def main():
     del s2
 
     # end to end through the C-ABI with host buffers: H2D of the state,
-    # one step, D2H of the state, every step
+    # one step, D2H of the state, every step.  The upload restores the state
+    # the solver produced (kind "restore": the same validating copy kernel,
+    # the realizability check reported but not enforced, because the scheme
+    # may leave cells marginally outside sigma <= 1)
     e2e = None
     if not args.no_e2e:
         host_in = torch.from_numpy(s.get_moments("conserved")).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         ne = max(2, min(args.steps, 5))
-        s.set_state(host_in.numpy(), kind="conserved")
+        s.set_state(host_in.numpy(), kind="restore")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ne):
-            s.set_state(host_in.numpy(), kind="conserved")
+            s.set_state(host_in.numpy(), kind="restore")
             s.step(1, float("inf"), sync=False)
             s.get_moments("conserved", out=host_out.numpy())
         el = time.perf_counter() - t0
@@ -566,24 +828,28 @@ def main():
     if rank != 0:
         return
     hbm, src = peaks()
-    bpc = BYTES_PER_CELL_UPDATE[(args.precision, planar)]
+    bpc = BYTES_PER_CELL_UPDATE[args.precision]
     kt = statistics.mean(per) * 1e-3        # one step = both stage launches of the kernel
     achieved = bpc * ncell / kt / 1e9
-    bpc2 = BYTES_PER_CELL_UPDATE[(other, planar2)]
+    bpc_p = PLANAR_BYTES_PER_CELL_UPDATE[args.precision] if planar else bpc
+    bpc2 = BYTES_PER_CELL_UPDATE[other]
     ach2 = bpc2 * ncell / (statistics.mean(per2) * 1e-3) / 1e9
+    traffic = TRAFFIC_PER_CELL_UPDATE.get((args.precision, planar))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 (+f64 accumulator, f64 closure islands)",
         "data": "synthetic",
-        "config": workload_config(n, args.precision, world, planar),
+        "config": workload_config(n, args.precision, world, planar, args.prerun),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
-                     "traffic": (TRAFFIC_PER_CELL_UPDATE[(args.precision, planar)] * ncell
-                                 if (args.precision, planar) in TRAFFIC_PER_CELL_UPDATE else None),
+                     "traffic": traffic * ncell if traffic else None,
                      "kernel": KERNEL[(args.precision, planar)], "peak_source": src,
-                     "bytes_per_cell_update": bpc},
+                     "bytes_per_cell_update": bpc,
+                     "planar_basis": {"bytes_per_cell_update": bpc_p,
+                                      "achieved": bpc_p * ncell / kt / 1e9,
+                                      "frac": bpc_p * ncell / kt / 1e9 / hbm}},
         "roofline_issue": issue_roofline(args.precision, planar, ncell, kt, clk),
         "compare": {"precision": other, "value": other_value, "unit": UNIT, "steps": csteps,
                     "ms_per_step": total2 / csteps, "speedup_of_headline": value / other_value,
@@ -595,8 +861,9 @@ def main():
         "clocks": clk.summary(),
         "diag": {"t": d["t"], "steps": d["steps"], "min_sigma": d["min_sigma"],
                  "n_sigma_below_lim": d["n_sigma_below_lim"], "n_nonfinite": d["n_nonfinite"],
-                 "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"])
-                 if d["n_closures"] else None},
+                 "n_nonpositive": d["n_nonpositive"], "timed_steps_from": d0["steps"] + 1,
+                 "fp64_closure_share_timed": fp64_share},
+        "developed_state": developed_leg,
     }
     if not args.no_batch:
         out["batch"] = bench_batch(mx, wl, stream, world, args.batch_t_end)
@@ -604,8 +871,12 @@ def main():
         out["adjoint"] = bench_adjoint(world)
     if not args.no_jet:
         out["single_jet"] = bench_single_jet(mx, wl, stream, world)
+    if not args.no_l1:
+        out["mixed_l1_per_field"] = bench_mixed_l1(mx, wl, stream)
+    if not args.no_dt_history:
+        out["crossing_jets_dt"] = bench_dt_history(mx, wl, stream)
     if not args.no_cpu and world == 1:
-        out["cpu_baseline"] = cpu_baseline(wl)
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_full)
     print(json.dumps(finite_json(out)), flush=True)
 
 

@@ -179,9 +179,18 @@ mxe_status mxe_set_relaxation(mxe_ctx *ctx, int model, double tau_ref, double rh
 mxe_status mxe_set_source_scheme(mxe_ctx *ctx, int scheme);
 
 /* March until t_end or max_steps steps, with dt = min(cfl/max_rate, t_end-t)
- * recomputed every step on the device.  t_out / steps_out (may be NULL)
- * receive the new time and the steps taken in this call; passing either
- * synchronises.  Returns MXE_ENONFINITE if a non-finite value appeared. */
+ * recomputed every step on the device (Sec. 3; the CFL reading of the
+ * oracle).  t_out / steps_out (may be NULL) receive the new time and the
+ * steps taken in this call; passing either synchronises, and so does every
+ * chunk of a call with max_steps > 4.  Returns MXE_ENONFINITE if a
+ * non-finite value appeared, MXE_EUNREALIZABLE if a cell lost positivity
+ * (rho <= 0 or a diagonal pressure <= 0: the scheme does not guarantee
+ * realizability, and the wave speeds of such a state are undefined) or if
+ * the CFL step size collapsed to zero before t_end (a non-finite wave
+ * speed); the state is left as the last step wrote it.  These are found
+ * from the device clock, i.e. when the call synchronises; an asynchronous
+ * call (max_steps <= 4, no t_out / steps_out) reports them on the next
+ * synchronising call or through mxe_get_diagnostics. */
 mxe_status mxe_step(mxe_ctx *ctx, int max_steps, double t_end, double *t_out,
                     int *steps_out);
 

@@ -1019,9 +1019,14 @@ static mxe_status tube_status(mxe_ctx* c, double* t0, long long* steps0) {
     CK(cudaStreamSynchronize(c->stream));
     if (t0) *t0 = h[0].t;
     if (steps0) *steps0 = h[0].steps;
-    for (int b = 0; b < c->ntubes; ++b)
+    for (int b = 0; b < c->ntubes; ++b) {
         if (h[b].status & ST_NONFINITE)
             return fail(c, MXE_ENONFINITE, "tube %d: non-finite state at t = %g", b, h[b].t);
+        if (h[b].status & ST_NONPOSITIVE)
+            return fail(c, MXE_EUNREALIZABLE,
+                        "tube %d: a cell lost positivity (rho <= 0 or a diagonal pressure <= 0) "
+                        "at t = %g", b, h[b].t);
+    }
     return MXE_OK;
 }
 
@@ -1057,8 +1062,11 @@ extern "C" mxe_status mxe_step(mxe_ctx* c, int max_steps, double t_end, double* 
         if (s != MXE_OK) return s;
         st0 = h.steps;
     }
-    // launch in chunks; a step past t_end is a no-op on the device
+    // launch in chunks; a step past t_end is a no-op on the device, and so
+    // is a step whose CFL size is zero (a non-finite wave speed somewhere)
     int done = 0, chunk = 4;
+    bool have = false, stalled = false;
+    long long prev = -1;
     while (done < max_steps) {
         int n = std::min(chunk, max_steps - done);
         for (int i = 0; i < n; ++i) {
@@ -1069,16 +1077,34 @@ extern "C" mxe_status mxe_step(mxe_ctx* c, int max_steps, double t_end, double* 
         if (done >= max_steps) break;
         s = read_clock_2d(c, &h);
         if (s != MXE_OK) return s;
-        if (h.status & ST_NONFINITE) break;
+        have = true;
+        if (h.status & (ST_NONFINITE | ST_NONPOSITIVE)) break;
         if (!(h.t[c->slot] < t_end)) break;
+        if (h.steps == prev) {                // no step advanced the clock
+            stalled = true;
+            break;
+        }
+        prev = h.steps;
         chunk = std::min(chunk * 2, 256);
     }
     if (want) {
         s = read_clock_2d(c, &h);
         if (s != MXE_OK) return s;
+        have = true;
         if (t_out) *t_out = h.t[c->slot];
         if (steps_out) *steps_out = (int)(h.steps - st0);
+        if (h.steps - st0 < done && h.t[c->slot] < t_end) stalled = true;
+    }
+    if (have) {
         if (h.status & ST_NONFINITE) return fail(c, MXE_ENONFINITE, "non-finite state");
+        if (h.status & ST_NONPOSITIVE)
+            return fail(c, MXE_EUNREALIZABLE,
+                        "a cell lost positivity (rho <= 0 or a diagonal pressure <= 0) by t = %g "
+                        "after %lld steps; its wave speeds are undefined", h.t[c->slot], h.steps);
+        if (stalled)
+            return fail(c, MXE_EUNREALIZABLE,
+                        "the CFL step size collapsed to zero at t = %g after %lld steps (a wave "
+                        "speed is not finite)", h.t[c->slot], h.steps);
     }
     return MXE_OK;
 }
