@@ -297,10 +297,15 @@ mxe_status mxe_get_dt_history(mxe_ctx *ctx, long long n, double *out);
  * with the step sizes held fixed.  mxe_adjoint_record advances the current
  * state by n steps of the given sizes (as mxe_step_dt) and keeps U^n and,
  * for RK2, U* of every step on the device (the tape: 2 n copies of the
- * state; replaces the previous tape).  The context must hold a planar
- * state (u_z, P_xz, P_yz, q_z zero) and planar boundary states.
- * Errors: MXE_ESTATE (not an FP64 2D 14-moment planar context, no state),
- * MXE_EINVAL (n < 1, dt <= 0), MXE_ENOMEM / MXE_ECUDA. */
+ * state; replaces the previous tape).  dts == NULL: n steps at the CFL
+ * step size instead (as mxe_step), recorded as they are taken, so that a
+ * forward run can keep its own tape; their sizes are read from the dt
+ * history, which must cover them (mxe_set_dt_history), and the call
+ * synchronises.  The context must hold a planar state (u_z, P_xz, P_yz,
+ * q_z zero) and planar boundary states.
+ * Errors: MXE_ESTATE (not an FP64 2D 14-moment planar context, no state,
+ * dt history too short), MXE_EINVAL (n < 1, dt <= 0), MXE_EUNREALIZABLE /
+ * MXE_ENONFINITE (CFL recording: as mxe_step), MXE_ENOMEM / MXE_ECUDA. */
 mxe_status mxe_adjoint_record(mxe_ctx *ctx, int n, const double *dts);
 
 /* Reverse sweep over the tape (hand-written reverse mode of primitive
@@ -311,7 +316,11 @@ mxe_status mxe_adjoint_record(mxe_ctx *ctx, int n, const double *dts);
  * state before the first.  Adds to gbar ([4][1 + MAX_SPANS][14] host
  * array: side, slot 0 = base Dirichlet state / 1 + n = span n, primitive
  * field) the adjoint of the imposed primitive states, and to *taubar the
- * adjoint of tau_ref (either may be NULL).  Synchronises. */
+ * adjoint of tau_ref (either may be NULL).  Synchronises.  MXE_ENONFINITE
+ * if the adjoint state or these adjoints are not finite (the FP32
+ * face-state reverse can leave its range); gbar and *taubar are then left
+ * unchanged, so that the caller can sweep again from a kept copy of ubar
+ * with the FP64 reverse. */
 mxe_status mxe_adjoint_run(mxe_ctx *ctx, double *ubar, int on_device, double *gbar,
                            double *taubar);
 

@@ -341,7 +341,11 @@ def mxe_set_adjoint_precision(ctx, precision):
                                                 else int(precision)))
 
 
-def mxe_adjoint_record(ctx, dts):
+def mxe_adjoint_record(ctx, dts, n=None):
+    """dts: step sizes to replay, or None to record n CFL steps."""
+    if dts is None:
+        _check(ctx, lib().mxe_adjoint_record(ctx, int(n), None))
+        return
     d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
     _check(ctx, lib().mxe_adjoint_record(ctx, len(d), C.c_void_p(d.ctypes.data)))
 
@@ -458,8 +462,10 @@ class Solver:
     def set_adjoint_precision(self, precision):
         mxe_set_adjoint_precision(self.ctx, precision)
 
-    def adjoint_record(self, dts):
-        mxe_adjoint_record(self.ctx, dts)
+    def adjoint_record(self, dts, n=None):
+        """Replay the given step sizes keeping the tape, or (dts None)
+        march n CFL steps keeping the tape (needs the dt history)."""
+        mxe_adjoint_record(self.ctx, dts, n)
 
     def adjoint_run(self, ubar):
         return mxe_adjoint_run(self.ctx, ubar)

@@ -11,7 +11,9 @@ state every ``ckpt`` steps (device tensors).  Backward: for each segment,
 last first, restore its checkpoint, replay it with ``mxe_adjoint_record``
 (which keeps U^n and U* of each step on the device) and sweep it in reverse
 with ``mxe_adjoint_run``; the adjoint state is carried from segment to
-segment on the device.  The C library returns the adjoints of the imposed
+segment on the device.  When the whole tape fits in device memory (GB300:
+288 GB; 2 x 500 states of 29 MB for the 512^2 configuration) the forward
+march records it directly and the backward sweeps it without replaying.  The C library returns the adjoints of the imposed
 inflow primitive states and of tau_ref; the inflow velocity of a jet is
 M sqrt(gamma T_jet) along its slot normal, which maps the first onto the
 Mach numbers.
@@ -25,28 +27,40 @@ import math
 
 import numpy as np
 
-from . import (BC_DIRICHLET, GHOST_SLOTS, TAU_HARDSPHERE, XLO, YLO, Solver)
+from . import (BC_DIRICHLET, ENONFINITE, GHOST_SLOTS, TAU_HARDSPHERE, XLO, YLO,
+                MaxentError, Solver)
 from . import workloads as wl
 
 GAMMA = 5.0 / 3.0
 
 
 class JetsProblem:
-    """Crossed jets on [0,1]^2, n x n cells; probe = mean density over the
-    probe x probe cells centred on (0.5, 0.5).  Parameters p = (Mach of the
-    left jet, Mach of the bottom jet, tau_ref).  initial: "developed" (the
-    synthetic developed crossed-jets state of the throughput benchmark, both
-    beams already across the domain), "rest" (background at rest, the start
-    of a simulation) or "smooth" (a smooth, resolved non-equilibrium gas into
+    """Crossed jets on [0,1]^2, n x n cells; probe = mean density over a
+    block of probe x probe cells: centred on (0.5, 0.5), where the jets
+    cross (probe_at="centre"), or against the left wall centred on the left
+    inflow slot (probe_at="left_slot"), which the left jet reaches from the
+    first steps.  Parameters p = (Mach of the left jet, Mach of the bottom
+    jet, tau_ref).  initial: "developed" (the synthetic developed
+    crossed-jets state of the throughput benchmark, both beams already
+    across the domain), "rest" (background at rest, the start of a
+    simulation) or "smooth" (a smooth, resolved non-equilibrium gas into
     which the jets blow)."""
 
     def __init__(self, n=512, Kn=0.1, nsteps=500, ckpt=50, probe=32, mach=(3.0, 3.0),
                  initial="developed", order=2, relax=True, adjoint_precision="fp64",
-                 adjoint_limiter="exact"):
+                 adjoint_limiter="exact", probe_at="centre", tape="auto"):
         if nsteps % ckpt:
             raise ValueError("nsteps must be a multiple of ckpt")
         if initial not in ("developed", "rest", "smooth"):
             raise ValueError("initial must be 'developed', 'rest' or 'smooth'")
+        if tape not in ("auto", "keep", "recompute"):
+            raise ValueError("tape must be 'auto', 'keep' or 'recompute'")
+        # "keep": the forward run records the whole tape (U^n, U* of every
+        # step) in device memory and the backward sweeps it directly;
+        # "recompute": checkpoints every ckpt steps, each segment replayed
+        # before its sweep; "auto": keep when the tape fits in half of the
+        # free device memory
+        self.tape = tape
         self.initial_kind = initial
         self.order, self.relax = order, relax
         self.adjoint_precision = adjoint_precision
@@ -57,7 +71,12 @@ class JetsProblem:
         self.setup = wl.jets_setup(mach=mach, Kn=Kn)
         self.p0 = (float(mach[0]), float(mach[1]), float(self.setup["tau_ref"]))
         lo = (n - probe) // 2
-        self.probe = (lo, lo + probe)
+        if probe_at not in ("centre", "left_slot"):
+            raise ValueError("probe_at must be 'centre' or 'left_slot'")
+        self.probe_at = probe_at
+        # probe block: rows (y) [r0, r1), columns (x) [c0, c1)
+        self.probe = (lo, lo + probe, lo, lo + probe) if probe_at == "centre" else \
+            (lo, lo + probe, 0, probe)
         self.T_jet = self.setup["T_ref"]
 
     def params0(self):
@@ -88,8 +107,8 @@ class JetsProblem:
 
     def probe_of(self, U):
         """mean density over the probe block of a conserved state (14, n, n)"""
-        a, b = self.probe
-        return U[0, a:b, a:b].mean()
+        r0, r1, c0, c1 = self.probe
+        return U[0, r0:r1, c0:c1].mean()
 
     def dmach(self):
         """d(imposed u_normal)/dM for each jet"""
@@ -107,13 +126,34 @@ def run_fixed(prob: JetsProblem, p, dts):
     return float(prob.probe_of(U))
 
 
+def tape_bytes(prob: JetsProblem):
+    """device memory of the whole tape: U^n and U* of every step"""
+    return 2 * prob.nsteps * 14 * prob.n * (prob.n + 32) * 8
+
+
+def keeps_tape(prob: JetsProblem):
+    if prob.tape != "auto":
+        return prob.tape == "keep"
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return tape_bytes(prob) <= 0.5 * free
+
+
 def forward_checkpointed(prob: JetsProblem, p):
-    """March nsteps CFL steps from the background; returns (J, checkpoints,
-    dts, solver)."""
+    """March nsteps CFL steps from the initial state; returns (J,
+    checkpoints, dts, solver).  When the tape is kept (keeps_tape) the
+    march records it and there are no checkpoints."""
     import torch
     s = prob.solver(p)
     s.set_state(prob.initial())
     s.set_dt_history(prob.nsteps)
+    prob.tape_kept = keeps_tape(prob)
+    if prob.tape_kept:
+        s.adjoint_record(None, prob.nsteps)
+        dts = s.dt_history(prob.nsteps)
+        U = torch.empty((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
+        s.get_moments("conserved", out=U)
+        return float(prob.probe_of(U)), [], dts, s
     ckpts = []
     for _ in range(prob.nsteps // prob.ckpt):
         U = torch.empty((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
@@ -133,22 +173,28 @@ def backward_checkpointed(prob: JetsProblem, s: Solver, ckpts, dts, gJ=1.0):
     again with the FP64 reverse from the same incoming adjoint; the number of
     such segments is left in prob.fp64_fallbacks."""
     import torch
-    a, b = prob.probe
+    r0, r1, c0, c1 = prob.probe
     ubar = torch.zeros((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
-    ubar[0, a:b, a:b] = gJ / float((b - a) * (b - a))
+    ubar[0, r0:r1, c0:c1] = gJ / float((r1 - r0) * (c1 - c0))
     torch.cuda.synchronize()          # written on torch's stream, read on the library's
     G = np.zeros((4, GHOST_SLOTS, 14))
     tb = 0.0
     mixed = prob.adjoint_precision == "mixed"
     prob.fp64_fallbacks = 0
-    for k in range(len(ckpts) - 1, -1, -1):
-        s.set_state(ckpts[k], kind="restore")
-        s.adjoint_record(dts[k * prob.ckpt:(k + 1) * prob.ckpt])
+    # the kept tape is one segment of all the steps; otherwise replay each
+    # checkpointed segment, last first
+    segments = [None] if getattr(prob, "tape_kept", False) else range(len(ckpts) - 1, -1, -1)
+    for k in segments:
+        if k is not None:
+            s.set_state(ckpts[k], kind="restore")
+            s.adjoint_record(dts[k * prob.ckpt:(k + 1) * prob.ckpt])
         keep = ubar.clone() if mixed else None
         torch.cuda.synchronize()
-        g, t = s.adjoint_run(ubar)
-        if mixed and not (np.isfinite(g).all() and np.isfinite(t)
-                          and bool(torch.isfinite(ubar).all())):
+        try:
+            g, t = s.adjoint_run(ubar)
+        except MaxentError as e:   # the FP32 reverse left its range: sweep again in FP64
+            if not mixed or e.status != ENONFINITE:
+                raise
             ubar.copy_(keep)
             torch.cuda.synchronize()
             s.set_adjoint_precision("fp64")

@@ -670,15 +670,26 @@ extern "C" __global__ void mxe_adj_ghosts(const AdjArgs a) {
 }
 
 // dense (14, ny, nx) <-> pitched 14-field layout
-extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g, int to_pitched) {
+// Dense (14, ny, nx) <-> pitched layout of an adjoint state.  Unpacking
+// (to_pitched = 0) also sets *nonfinite when a value is not finite (the
+// FP32 face-state reverse can leave its range), if nonfinite is given.
+extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g, int to_pitched,
+                                        unsigned long long* nonfinite) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= g.nx) return;
+    bool bad = false;
     for (int k = 0; k < 14; ++k) {
         const long long d = ((long long)k * g.ny + j) * g.nx + i;
         const long long p = (long long)k * g.fstride + (long long)j * g.pitch + i;
-        if (to_pitched) pitched[p] = dense[d];
-        else const_cast<double*>(dense)[d] = pitched[p];
+        if (to_pitched) {
+            pitched[p] = dense[d];
+        } else {
+            const double v = pitched[p];
+            const_cast<double*>(dense)[d] = v;
+            bad |= !isfinite(v);
+        }
     }
+    if (bad && nonfinite) atomicOr(nonfinite, 1ull);
 }
 
 size_t adj_args_size() { return sizeof(AdjArgs); }

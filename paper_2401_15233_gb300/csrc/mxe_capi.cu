@@ -60,8 +60,8 @@ cudaError_t adj_stage(const double* U, const double* V, double coef, const doubl
                       double* gbar, double* taubar, const Grid2D& g, const ParamsT<double>& p,
                       bool f32, float* f32buf, bool frozen_phi, cudaStream_t st);
 long long adj_f32_floats(const Grid2D& g);
-extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g,
-                                        int to_pitched);
+extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g, int to_pitched,
+                                        unsigned long long* nonfinite);
 size_t tubes_mixed_smem(bool planar, int nt);
 int tile_x();
 int tile_y();
@@ -1363,7 +1363,7 @@ static mxe_status adjoint_ready(mxe_ctx* c) {
         CK(cudaMalloc(&c->adjCy, sizeof(double) * 4 * NP * (long long)(c->g.ny + 1) * c->g.nx));
         CK(cudaMalloc(&c->adjA, sizeof(double) * c->nelem));
         CK(cudaMalloc(&c->adjB, sizeof(double) * c->nelem));
-        CK(cudaMalloc(&c->adjG, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1)));
+        CK(cudaMalloc(&c->adjG, sizeof(double) * (4 * GHOST_SLOTS * 14 + 2)));   // + tau, flag
     }
     if (c->adj_f32 && !c->adjF) CK(cudaMalloc(&c->adjF, sizeof(float) * adj_f32_floats(c->g)));
     return MXE_OK;
@@ -1377,11 +1377,27 @@ static Grid2D adj_grid(const mxe_ctx* c) {
 
 extern "C" mxe_status mxe_adjoint_record(mxe_ctx* c, int n, const double* dts) {
     if (!c) return MXE_EINVAL;
-    if (n < 1 || !dts) return fail(c, MXE_EINVAL, "need n >= 1 step sizes");
-    for (int i = 0; i < n; ++i)
-        if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return fail(c, MXE_EINVAL, "dt[%d] <= 0", i);
+    if (n < 1) return fail(c, MXE_EINVAL, "need n >= 1 steps");
+    if (dts)
+        for (int i = 0; i < n; ++i)
+            if (!(dts[i] > 0.0) || !std::isfinite(dts[i]))
+                return fail(c, MXE_EINVAL, "dt[%d] <= 0", i);
     mxe_status s = adjoint_ready(c);
     if (s != MXE_OK) return s;
+    // dts == NULL: n steps at the CFL step size, recorded as they are taken;
+    // their sizes come back through the dt history
+    long long steps0 = 0;
+    if (!dts) {
+        DevClock h{};
+        s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        steps0 = h.steps;
+        if (!c->dth || steps0 + n > c->dth_cap)
+            return fail(c, MXE_ESTATE, "recording CFL steps needs a dt history of at least "
+                                       "%lld entries (mxe_set_dt_history)", steps0 + n);
+        if (h.status & (ST_NONFINITE | ST_NONPOSITIVE))
+            return fail(c, MXE_EUNREALIZABLE, "the state is not finite or not positive");
+    }
     const bool rk2 = c->cfg.integrator == MXE_RK2;
     const long long need = (long long)n * (rk2 ? 2 : 1);
     if (need > c->tape_cap) {
@@ -1396,19 +1412,33 @@ extern "C" mxe_status mxe_adjoint_record(mxe_ctx* c, int n, const double* dts) {
         double* un = c->tape + c->nelem * (long long)(rk2 ? 2 * i : i);
         CK(cudaMemcpyAsync(un, c->U, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
                            c->stream));
-        s = launch_2d_step(c, INFINITY, dts[i], rk2 ? un + c->nelem : nullptr, true);
+        s = dts ? launch_2d_step(c, INFINITY, dts[i], rk2 ? un + c->nelem : nullptr, true)
+                : launch_2d_step(c, INFINITY, 0.0, rk2 ? un + c->nelem : nullptr, false);
         if (s != MXE_OK) return s;
     }
-    // the replay skipped the CFL rate: form it once for the final state
-    {
+    if (dts) {
+        // the replay skipped the CFL rate: form it once for the final state
         DevClock* ck = c->clk;
         CK(cudaMemsetAsync(&ck->rate[c->slot], 0, sizeof(unsigned long long), c->stream));
         dim3 grid((c->g.nx + 255) / 256, c->g.ny);
         mxe_rate14_2d_planar<<<grid, 256, 0, c->stream>>>(c->U, c->g, c->sp, c->clk, c->slot);
         CK(cudaGetLastError());
+        c->tape_dt.assign(dts, dts + n);
+    } else {
+        DevClock h{};
+        s = read_clock_2d(c, &h);
+        if (s != MXE_OK) return s;
+        if (h.status & ST_NONFINITE) return fail(c, MXE_ENONFINITE, "non-finite state");
+        if (h.status & ST_NONPOSITIVE)
+            return fail(c, MXE_EUNREALIZABLE, "a cell lost positivity while recording");
+        if (h.steps - steps0 != n)
+            return fail(c, MXE_EUNREALIZABLE, "the CFL step size collapsed to zero while "
+                                              "recording (%lld of %d steps)", h.steps - steps0, n);
+        c->tape_dt.resize(n);
+        CK(cudaMemcpy(c->tape_dt.data(), c->dth + steps0, sizeof(double) * n,
+                      cudaMemcpyDeviceToHost));
     }
     c->tape_n = n;
-    c->tape_dt.assign(dts, dts + n);
     return MXE_OK;
 }
 
@@ -1428,10 +1458,11 @@ extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, d
     const Grid2D g = adj_grid(c);
     const dim3 pg((g.nx + 127) / 128, g.ny);
     CK(cudaMemsetAsync(c->adjA, 0, sizeof(double) * c->nelem, c->stream));
-    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(src, c->adjA, g, 1);
-    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1), c->stream));
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(src, c->adjA, g, 1, nullptr);
+    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 2), c->stream));
     double* gb = c->adjG;
     double* tb = c->adjG + 4 * GHOST_SLOTS * 14;
+    unsigned long long* nonfinite = (unsigned long long*)(c->adjG + 4 * GHOST_SLOTS * 14 + 1);
     const ParamsT<double> p = make_params<double>(c->sp, c->rp);
     const bool rk2 = c->cfg.integrator == MXE_RK2;
     for (int i = c->tape_n - 1; i >= 0; --i) {
@@ -1456,13 +1487,19 @@ extern "C" mxe_status mxe_adjoint_run(mxe_ctx* c, double* ubar, int on_device, d
         if (e != cudaSuccess) return fail(c, MXE_ECUDA, "adjoint stage: %s", cudaGetErrorString(e));
     }
     double* dst = on_device ? ubar : c->stage;
-    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, c->adjA, g, 0);
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, c->adjA, g, 0, nonfinite);
     CK(cudaGetLastError());
     if (!on_device)
         CK(cudaMemcpyAsync(ubar, c->stage, bytes, cudaMemcpyDeviceToHost, c->stream));
-    double hg[4 * GHOST_SLOTS * 14 + 1];
+    double hg[4 * GHOST_SLOTS * 14 + 2];
     CK(cudaMemcpyAsync(hg, c->adjG, sizeof hg, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    bool finite = std::isfinite(hg[4 * GHOST_SLOTS * 14]);
+    for (int k = 0; k < 4 * GHOST_SLOTS * 14; ++k) finite = finite && std::isfinite(hg[k]);
+    unsigned long long flag;
+    std::memcpy(&flag, &hg[4 * GHOST_SLOTS * 14 + 1], sizeof flag);
+    if (flag || !finite)     // gbar, taubar untouched: the caller may sweep again
+        return fail(c, MXE_ENONFINITE, "the adjoint left the finite range");
     if (gbar)
         for (int k = 0; k < 4 * GHOST_SLOTS * 14; ++k) gbar[k] += hg[k];
     if (taubar) *taubar += hg[4 * GHOST_SLOTS * 14];
@@ -1494,9 +1531,9 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
     }
     CK(cudaMemsetAsync(Up, 0, sizeof(double) * c->nelem, c->stream));
     CK(cudaMemsetAsync(Vp, 0, sizeof(double) * c->nelem, c->stream));
-    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(su, Up, g, 1);
-    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(sv, Vp, g, 1);
-    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 1), c->stream));
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(su, Up, g, 1, nullptr);
+    mxe_adj_pack<<<pg, 128, 0, c->stream>>>(sv, Vp, g, 1, nullptr);
+    CK(cudaMemsetAsync(c->adjG, 0, sizeof(double) * (4 * GHOST_SLOTS * 14 + 2), c->stream));
     const ParamsT<double> p = make_params<double>(c->sp, c->rp);
     double* Op = nullptr;
     CK(cudaMalloc(&Op, sizeof(double) * c->nelem));
@@ -1505,7 +1542,7 @@ extern "C" mxe_status mxe_adjoint_residual(mxe_ctx* c, const double* U, const do
                               c->adjF, c->adj_frozen, c->stream);
     if (e == cudaSuccess) {
         double* dst = on_device ? out : tmpU;
-        mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0);
+        mxe_adj_pack<<<pg, 128, 0, c->stream>>>(dst, Op, g, 0, nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess && !on_device)
             e = cudaMemcpyAsync(out, tmpU, bytes, cudaMemcpyDeviceToHost, c->stream);

@@ -105,9 +105,10 @@ def test_adjoint_steps_dot_product(mx, orc, smooth):
         assert abs(lhs - rhs) <= 1e-8 * (abs(lhs) + 1e-300), (name, lhs, rhs)
 
 
+@pytest.mark.parametrize("tape", ["keep", "recompute"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("initial", ["rest", "smooth"])
-def test_adjoint_probe_gradient_vs_fd(mx, initial, precision):
+def test_adjoint_probe_gradient_vs_fd(mx, initial, precision, tape):
     """Crossed jets (64^2, 200 RK2 steps, checkpoints every 40): gradient of
     the probe-mean density w.r.t. both Mach numbers and tau_ref against
     central differences of the frozen-dt map.  First-order reconstruction:
@@ -116,12 +117,16 @@ def test_adjoint_probe_gradient_vs_fd(mx, initial, precision):
     of fields whose differences are near round-off makes finite differences
     diverge as h -> 0); there the adjoint is checked against the oracle's
     tangent instead (test_adjoint_steps_dot_product).  precision "mixed":
-    the face states reversed in FP32 from the FP64 tape."""
+    the face states reversed in FP32 from the FP64 tape.  tape "keep": the
+    forward march records the whole tape; "recompute": checkpoints every 40
+    steps, each segment replayed before its sweep (the two give the same
+    gradient up to the order of the segment sums)."""
     from paper_2401_15233_gb300 import adjoint as ad
     prob = ad.JetsProblem(n=64, nsteps=200, ckpt=40, probe=8, initial=initial, order=1,
-                          adjoint_precision=precision)
+                          adjoint_precision=precision, tape=tape)
     p0 = prob.params0()
     J, ckpts, dts, s = ad.forward_checkpointed(prob, p0)
+    assert prob.tape_kept == (tape == "keep") and len(ckpts) == (0 if tape == "keep" else 5)
     g, _ = ad.backward_checkpointed(prob, s, ckpts, dts)
     assert abs(ad.run_fixed(prob, p0, dts) - J) <= 1e-14 * abs(J)
     hs = [1e-4, 1e-4, 1e-4 * p0[2]]
@@ -226,3 +231,78 @@ def test_adjoint_frozen_limiter_dot_product(mx, orc, smooth, precision):
         xe = aos_to_soa(ybar.copy())
         s.adjoint_run(xe)
         assert not np.allclose(xe, xbar, rtol=1e-6, atol=0)
+
+
+def test_adjoint_c5_size_slot_probe_vs_fd(mx):
+    """The adjoint configuration's size (512^2, 500 RK2 steps, checkpoints
+    every 50, Kn = 0.1, from rest) with the probe on the left inflow slot,
+    which the left jet crosses from the first steps (the configured probe at
+    the centre lies outside the inflows' domain of dependence for 500 steps:
+    signals travel ~0.1 of the domain, and adjoint and differences are both
+    exactly zero there).  First-order reconstruction (a smooth map, see
+    test_adjoint_probe_gradient_vs_fd): against central differences
+    (h = 1e-4, frozen dt) on the non-zero components, the FP64 reverse
+    within 1e-4 (measured 1.4e-5) and the FP32 face-state reverse within
+    1e-3 (measured 2.5e-4 on tau_ref: its FP32 face-state derivatives over
+    500 steps); the bottom jet's Mach number cannot reach the probe and its
+    derivative is zero in both."""
+    from paper_2401_15233_gb300 import adjoint as ad
+    prob = ad.JetsProblem(n=512, nsteps=500, ckpt=50, probe=32, initial="rest", order=1,
+                          probe_at="left_slot", tape="recompute")
+    p0 = prob.params0()
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        prob.adjoint_precision = prec
+        J, ckpts, dts, s = ad.forward_checkpointed(prob, p0)
+        grads[prec], _ = ad.backward_checkpointed(prob, s, ckpts, dts)
+        del s, ckpts
+    hs = [1e-4, 1e-4, 1e-4 * p0[2]]
+    fd = []
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = hs[k]
+        fd.append((ad.run_fixed(prob, p0 + e, dts) - ad.run_fixed(prob, p0 - e, dts)) / (2 * hs[k]))
+    fd = np.array(fd)
+    print(f"512^2 slot probe, first order: J {J:.10e}, fd {fd}, fp64 {grads['fp64']}, "
+          f"fp32 {grads['mixed']}")
+    nz = np.abs(fd) > 0
+    assert nz[0] and nz[2] and fd[1] == 0.0
+    for prec, g in grads.items():
+        tol = 1e-4 if prec == "fp64" else 1e-3
+        assert np.all(np.abs(g[nz] - fd[nz]) <= tol * np.abs(fd[nz])), (prec, g, fd)
+        assert np.all(np.abs(g[~nz]) <= 1e-12 * np.abs(fd).max()), (prec, g)
+
+
+def test_adjoint_muscl_dot_product_jets_in_probe(mx, orc):
+    """MUSCL (the configured scheme), the developed crossed-jets state with
+    the jets through the probe region, 64^2, 12 RK2 steps: the reverse sweep
+    against the oracle's independent forward-mode tangent, in a state, an
+    inflow-state and a tau_ref direction (<ybar, J x> = <J^T ybar, x>, 1e-8).
+    MUSCL's shared most-stringent limiter makes the map non-differentiable at
+    the scale of finite differences (they do not converge as h -> 0), so for
+    MUSCL this identity, not a difference quotient, is the check."""
+    n, nsteps = 64, 12
+    setup, U, rng = case(orc, n, 7, smooth=False)
+    cfg = jets_oracle_cfg(orc, n, n, setup)
+    dts = []
+    X = U
+    for _ in range(nsteps):
+        dts.append(orc.dt(cfg, X, 0.0, 10.0))
+        X = orc.step(cfg, X, dts[-1])
+    s = jets_gpu_solver(mx, n, n, setup)
+    s.set_state(aos_to_soa(U), kind="conserved")
+    s.adjoint_record(dts)
+    ybar = np.zeros(U.shape)
+    lo = (n - 16) // 2
+    ybar[lo:lo + 16, lo:lo + 16, 0] = 1.0 / 256.0      # the probe-mean density
+    xbar = aos_to_soa(ybar.copy())
+    gb, tb = s.adjoint_run(xbar)
+    xd, gd, td = directions(rng, U)
+    for name, (x, g, t) in {"state": (xd, gd * 0, 0.0), "inflow": (xd * 0, gd, 0.0),
+                            "tau": (xd * 0, gd * 0, td)}.items():
+        _, jx = orc.tangent_run(orc.tangent_cfg(cfg, d_states=g, d_tau_ref=t), U, x, dts)
+        lhs = float((ybar * jx).sum())
+        rhs = float((soa_to_aos(xbar) * x).sum() + (gb * g).sum() + tb * t)
+        print(f"MUSCL jets 64^2 {nsteps} steps <ybar, J x> {name}: {lhs:.12e} vs {rhs:.12e}")
+        assert lhs != 0.0
+        assert abs(lhs - rhs) <= 1e-8 * abs(lhs), (name, lhs, rhs)
