@@ -12,16 +12,17 @@
 // (a thread-block cluster of 1..8 CTAs) takes one tube at a time from a
 // device work queue whose order is longest-expected-work first, and marches
 // it to t_end on the tube's own clock.  Within a stage the team splits the
-// tube into chunks of NT-1 cells (chunk j belongs to CTA j mod team); a CTA
+// tube into chunks of NT-2 cells (chunk j belongs to CTA j mod team); a CTA
 // stages a chunk's primitives plus a 2-cell halo in shared memory, forms one
-// shared limiter per cell, evaluates one face per thread and updates its
-// cells.  Cluster barriers separate the stages; the team's CFL maximum and
+// shared limiter per cell (NT of them: one per thread), evaluates one face
+// per thread (planar states: both face states as one packed FP32 pair) and
+// updates its cells.  Cluster barriers separate the stages; the team's CFL maximum and
 // status bits are combined in the shared memory of CTA 0 of the cluster
 // (distributed shared memory).  Every wait in this file is a hardware
 // barrier reached by all threads of the team in the same order: there is no
 // spin loop.
 #include "mxe_internal.h"
-#include "mxe_mixed.cuh"
+#include "mxe_mixed_x2.cuh"
 
 namespace mxe {
 
@@ -65,8 +66,8 @@ __device__ __forceinline__ unsigned cl_ld(unsigned addr) {
 // ---- shared-memory layout of one CTA -------------------------------------
 template <int NF, int NT>
 struct TubeLayout {
-    static constexpr int C = NT - 1;              // cells per chunk
-    static constexpr int BOX = NT + 3;            // staged cells (chunk + 2 + 2)
+    static constexpr int C = NT - 2;              // cells per chunk (C + 2 limiters)
+    static constexpr int BOX = C + 4;             // staged cells (chunk + 2 + 2)
     static constexpr int FS = 2 * NF + 2;         // staged left face state
     static constexpr int W_OFF = 0;               // [NF][BOX] primitives
     static constexpr int F_OFF = W_OFF + NF * BOX;   // [NF][NT] face fluxes
@@ -96,34 +97,6 @@ __device__ __forceinline__ void load_w(const TubeMixedArgs& a, const float* Wt, 
     // written by other CTAs of the team in the previous stage: read from L2
 #pragma unroll
     for (int k = 0; k < PH::NF; ++k) Q[k] = __ldcg(Wt + (long long)k * n + gi);
-}
-
-// shared minmod / van Albada limiter of box cell c (fields k at stride BOX)
-template <int NF, int BOX>
-__device__ __forceinline__ float phi_1d(const float* W, int c, int lim) {
-    float phi = 1.0f;
-    const FlatRef<float> fr = flat_ref<NF>(W + c, BOX);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        const float* w = W + k * BOX + c;
-        float dm = w[0] - w[-1], dp = w[1] - w[0];
-        float pk;
-        if (dm * dp > 0.0f) {
-            if (lim == 1) {      // approximate quotient (2 ulp): the limiter is a ratio
-                pk = __fdividef(2.0f * dm * dp, dm * dm + dp * dp);
-            } else {
-                float am = fabsf(dm), ap = fabsf(dp);
-                pk = __fdividef(2.0f * fminf(am, ap), am + ap);
-            }
-        } else {
-            pk = (dm == 0.0f && dp == 0.0f) ? 1.0f : 0.0f;
-        }
-        if (pk < phi) {          // a flat field (phi_k = 1) never lowers phi
-            const float m = abs_max(dm, dp);
-            if (!(m <= FLAT_REL_F32 * fabsf(w[0]) || field_flat<NF>(fr, k, m))) phi = pk;
-        }
-    }
-    return phi;
 }
 
 // Face flux of the face between box cells cl = tid+1 and cr = tid+2; the
@@ -216,12 +189,17 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
         }
         __syncthreads();
         for (int i = tid; i < C + 2; i += NT)
-            ph[i] = p.order == 2 ? phi_1d<NF, BOX>(Wb, i + 1, p.limiter) : 0.0f;
+            ph[i] = p.order == 2 ? phi_one_m<NF, BOX>(Wb, i + 1, 1, p.limiter) : 0.0f;
         __syncthreads();
-        {
+        if (tid <= C) {                  // C + 1 faces
             float F[NF];
-            face_flux_1d<PH, NT, BOX>(Wb, tid + 1, ph[tid], ph[tid + 1], p, mp, a.sl64, a.kw64,
-                                      Ls + tid, F, nflag);
+            if constexpr (NF == NP) {
+                face_flux_x2<0, BOX>(Wb, tid + 1, 1, ph[tid], ph[tid + 1], p, mp, a.sl64,
+                                     a.kw64, F, nflag);
+            } else {
+                face_flux_1d<PH, NT, BOX>(Wb, tid + 1, ph[tid], ph[tid + 1], p, mp, a.sl64,
+                                          a.kw64, Ls + tid, F, nflag);
+            }
 #pragma unroll
             for (int k = 0; k < NF; ++k) Fb[k * NT + tid] = F[k];
         }
@@ -251,11 +229,15 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
                     PH::relax_prim(Wn, 1.0f / (1.0f + cdt / PH::tau(p, Wn)), N);
                 }
             } else {
+                // U += dU in FP64 (the conservation accumulator); a
+                // non-finite increment marks the state non-finite
                 bool bad = false;
                 double Un[NF];
 #pragma unroll
-                for (int k = 0; k < NF; ++k)
-                    Un[k] = v.U[(long long)PH::ufield(k) * n + i] + (double)dU[k];
+                for (int k = 0; k < NF; ++k) {
+                    Un[k] = v.U[(long long)PH::ufield(k) * n + i] + f32_to_f64_bits(dU[k]);
+                    bad |= !(fabsf(dU[k]) < __int_as_float(0x7f800000));
+                }
                 if (resync) {
                     double Q64[NF];
                     PH::cons2prim_fast(Un, Q64);
@@ -276,10 +258,7 @@ __device__ float tube_stage_m(const TubeMixedArgs& a, const TubeView& v, const M
                     for (int k = 0; k < NF; ++k) Un[k] += (double)((gm - 1.0f) * N[k]);
                 }
 #pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    v.U[(long long)PH::ufield(k) * n + i] = Un[k];
-                    bad |= !isfinite(Un[k]);
-                }
+                for (int k = 0; k < NF; ++k) v.U[(long long)PH::ufield(k) * n + i] = Un[k];
                 if (bad) status |= ST_NONFINITE;
                 if (PH::nonpositive(Wn)) status |= ST_NONPOSITIVE;
                 float r = PH::rate_x(Wn, p.sigma_lim, p.k_ws) * v.idx;
@@ -455,14 +434,14 @@ __device__ void tubes_mixed_body(const TubeMixedArgs& a, const ParamsT<float>& p
             ++steps;
             if (bst) break;          // team-uniform
         }
-        // face-state closures: 2 per face, NT faces per chunk and stage
+        // face-state closures: 2 per face, C + 1 faces per chunk and stage
         unsigned wf = __reduce_add_sync(0xffffffffu, nflag);
         if ((tid & 31) == 0 && wf) atomicAdd(&s_cnt, wf);
         __syncthreads();
         if (tid == 0) {
             unsigned nch = 0;
             for (int c0 = (int)rank * C; c0 < n; c0 += (int)team * C) ++nch;
-            atomicAdd(&ck->n_face, (unsigned long long)nface * nch * 2ull * NT);
+            atomicAdd(&ck->n_face, (unsigned long long)nface * nch * 2ull * (C + 1));
             if (s_cnt) atomicAdd(&ck->n_face64, (unsigned long long)s_cnt);
             if (rank == 0) {
                 ck->t = t;
