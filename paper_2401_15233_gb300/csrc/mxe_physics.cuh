@@ -767,10 +767,15 @@ __device__ __forceinline__ void relax14_prim(T* W, T g, T* N) {
 // with s = P (5-moment) or s = tr P = 3p (14-moment):
 //   m <= T rho;  m^2 rho <= T^2 p;  m <= T p;  m^2 rho <= T^2 p^3;  m rho <= T p^2.
 // The FP32 primitives of the mixed path take the same test and also count
-// a field as flat when m <= 2^-16 |Q_i,k| (128 to 256 FP32 ulps of the
-// centre value): in a uniform non-zero field the FP32 flux differences
-// leave a random walk of a few ulps per sqrt(step) in the FP64 state, which
-// the natural-scale bound alone would let through.
+// a field as flat when m <= 2^-20 |Q_i,k| (8 to 16 FP32 ulps of the centre
+// value): in a uniform non-zero field the FP32 flux differences leave a
+// random walk of a few ulps in the FP64 state, which the natural-scale bound
+// alone would let through.  The factor is the smallest power of two at
+// which the mixed path stays second order on a density wave at uniform
+// velocity and pressure (2^-21, 2^-22 and 2^-24 measured first order); a
+// larger one also treats shallow genuine extrema as flat, which showed as
+// error on long near-collisionless runs (2^-16: 1.4e-4 density L1 on the
+// 4096-cell Sod tube at Kn = 10 to t = 0.2, against 3.8e-5 with 2^-20).
 template <class T>
 struct FlatConst;
 template <>
@@ -781,7 +786,7 @@ template <>
 struct FlatConst<float> {
     static constexpr float tol = 1e-10f;
 };
-constexpr float FLAT_REL_F32 = 1.52587890625e-5f;     // 2^-16
+constexpr float FLAT_REL_F32 = 9.5367431640625e-07f;   // 2^-20
 
 // scale class of field k in the 5-field, planar 10-field and general
 // 14-field primitive layouts: 0 rho, 1 velocity, 2 pressure tensor,

@@ -18,3 +18,29 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+# Config 2's oracle trajectories take minutes: when its test is collected,
+# start them in a spawn-started process pool right away (no GPU work is done
+# in the workers), so that they run while the rest of the suite does.
+_CONFIG2 = {}
+
+
+def pytest_collection_finish(session):
+    if any("test_gpu_zconfig2" in it.nodeid for it in session.items):
+        from tests._config2 import Runs
+        _CONFIG2["runs"] = Runs()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    runs = _CONFIG2.pop("runs", None)
+    if runs is not None:
+        runs.close()
+
+
+@pytest.fixture(scope="session")
+def config2_runs():
+    if "runs" not in _CONFIG2:
+        from tests._config2 import Runs
+        _CONFIG2["runs"] = Runs()
+    return _CONFIG2["runs"]
