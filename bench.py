@@ -45,14 +45,15 @@ UNIT = "cell-updates/s"
 BYTES_PER_CELL_UPDATE = {"fp64": 560.0, "mixed": 448.0}
 PLANAR_BYTES_PER_CELL_UPDATE = {"fp64": 400.0, "mixed": 360.0}
 # DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over the two stage launches of one step, 2048^2
-# crossed jets, 4.19e6 cells; scaled to the benchmark grid by cell count)
+# dram__bytes_write.sum over the two stage launches of step 1001 of the
+# crossed jets from rest at 2048^2, 4.19e6 cells; scaled to the benchmark grid
+# by cell count)
 TRAFFIC_PER_CELL_UPDATE = {("mixed", True): 342.4}
 # Issue-rate roofline of the mixed planar stage kernel (bound by instruction
 # issue, not by DRAM): thread instructions per cell-update over both stages
-# (ncu smsp__inst_executed.sum x 32 / cells, 2048^2 crossed jets) against
+# (ncu smsp__inst_executed.sum x 32 / cells, the same two launches) against
 # 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
-THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 5228.3}
+THREAD_INST_PER_CELL_UPDATE = {("mixed", True): 5269.2}
 KERNEL = {("fp64", False): "mxe_stage14_2d_f64", ("mixed", False): "mxe_stage14_2d_mixed_b3",
           ("fp64", True): "mxe_stage14_2d_f64_planar",
           ("mixed", True): "mxe_stage14_2d_mixed_planar_x2"}
