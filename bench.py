@@ -90,6 +90,9 @@ def parse():
     p.add_argument("--only", default=None, choices=["batch", "adjoint", "cpu", "l1", "dt"],
                    help="run one secondary leg alone (profiling runs)")
     p.add_argument("--batch-t-end", type=float, default=0.2)
+    p.add_argument("--batch-shape", default=None,
+                   help="block shape of the batched tubes as THREADSxCTAS (e.g. 256x8) "
+                        "instead of the autotuner's choice")
     p.add_argument("--adj-n", type=int, default=512)
     p.add_argument("--adj-steps", type=int, default=500)
     p.add_argument("--adj-ckpt", type=int, default=50)
@@ -486,7 +489,7 @@ def bench_dt_history(mx, wl, stream, n=1200, steps=10000):
             if d["n_closures"] else None}
 
 
-def bench_batch(mx, wl, stream, world, t_end=0.2):
+def bench_batch(mx, wl, stream, world, t_end=0.2, shape=None):
     """Batched 14-moment Sod tubes: 256 tubes of 512..8192 cells, Kn in
     [1e-3, 10], density ratio in [4, 20], each run to t = 0.2 in one persistent
     launch replayed from a CUDA graph, block shape from the autotuner.  Also
@@ -519,7 +522,12 @@ def bench_batch(mx, wl, stream, world, t_end=0.2):
         return e0.elapsed_time(e1), int((ncells * st).sum()), st
 
     b = make("mixed")
-    nt, cl, tune_ms = b.autotune(0.002)
+    if shape:
+        nt, cl = (int(x) for x in shape.lower().split("x"))
+        b.set_shape(nt, cl)
+        tune_ms = None
+    else:
+        nt, cl, tune_ms = b.autotune(0.002)
     b.run(10 ** 8, t_end)                 # warm-up: captures the graph for t_end
     b.set_state(b.pack(prims))            # back to t = 0 (same launch arguments: replay)
     ms, cu, st = timed_run(b, t_end)
@@ -742,7 +750,7 @@ def main():
     if args.only:
         stream = torch.cuda.Stream()
         if args.only == "batch":
-            leg = bench_batch(mx, wl, stream, world, args.batch_t_end)
+            leg = bench_batch(mx, wl, stream, world, args.batch_t_end, args.batch_shape)
         elif args.only == "cpu":
             leg = cpu_baseline(wl, args.cpu_full)
         elif args.only == "l1":
@@ -900,7 +908,7 @@ def main():
         "developed_state": developed_leg,
     }
     if not args.no_batch:
-        out["batch"] = bench_batch(mx, wl, stream, world, args.batch_t_end)
+        out["batch"] = bench_batch(mx, wl, stream, world, args.batch_t_end, args.batch_shape)
     if not args.no_adjoint:
         out["adjoint"] = bench_adjoint(world)
     if not args.no_jet:
