@@ -532,6 +532,7 @@ def bench_batch(mx, wl, stream, world, t_end=0.2, shape=None):
     b.set_state(b.pack(prims))            # back to t = 0 (same launch arguments: replay)
     ms, cu, st = timed_run(b, t_end)
     d = b.diagnostics()
+    teams, team_tubes, fill = b.layout()
     bw = make("mixed")
     bw.set_shape(nt, cl)
     bw.run(20, 0.2)
@@ -549,7 +550,9 @@ def bench_batch(mx, wl, stream, world, t_end=0.2, shape=None):
         "precision": "mixed", "value": world * cu / (ms * 1e-3), "unit": UNIT,
         "ms": ms, "cell_updates": cu, "cells": int(ncells.sum()),
         "steps_min": int(st.min()), "steps_max": int(st.max()),
-        "graph_launches": 1, "gpu_launches": 2,
+        "graph_launches": 1, "gpu_launches": 3 if fill else 2,
+        "layout": {"teams": teams, "team_tubes": team_tubes, "fill_ctas": fill,
+                   "fill_tubes": len(tubes) - team_tubes},
         "shape": {"threads_per_cta": nt, "ctas_per_team": cl, "autotune_ms_t0.002": tune_ms},
         "fp64_closure_share": (d["n_fp64_closures"] / d["n_closures"]) if d["n_closures"] else None,
         "n_nonfinite": d["n_nonfinite"], "n_nonpositive": d["n_nonpositive"],

@@ -261,7 +261,13 @@ mxe_status mxe_batch_set_relaxation(mxe_ctx *ctx, int tube, int model, double ta
 mxe_status mxe_batch_get_clock(mxe_ctx *ctx, double *t, long long *steps);
 
 /* Advance every tube until its own t reaches t_end or it has taken
- * max_steps steps in this call; one launch for the whole batch. */
+ * max_steps steps in this call.  MXE_FP64: one launch, one block per tube.
+ * MXE_MIXED: one persistent launch of teams of CTAs (clusters) over a work
+ * queue ordered by expected work (largest first); when the teams cannot use
+ * every CTA slot of the device (clusters are placed whole within a GPU
+ * processing cluster), a second, concurrent launch of single CTAs takes the
+ * smallest tubes (see mxe_batch_get_layout).  Results do not depend on which
+ * launch, team or CTA advances a tube. */
 mxe_status mxe_batch_run(mxe_ctx *ctx, int max_steps, double t_end);
 
 /* MXE_MIXED tube contexts: time every block shape (128 or 256 threads per
@@ -279,6 +285,16 @@ mxe_status mxe_batch_autotune(mxe_ctx *ctx, double t_probe, int *nt_out, int *cl
 /* MXE_MIXED tube contexts: set the block shape directly (nt in {128, 256},
  * cl in {1, 2, 4, 8}); the default is 128 x 1. */
 mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
+
+/* MXE_MIXED tube contexts: the launch layout mxe_batch_run uses with the
+ * current block shape (outputs may be NULL): teams of the team launch, the
+ * tubes handed to it (the largest, in work order), and the CTAs of the fill
+ * launch of single CTAs that takes the remaining tubes (0: no fill launch).
+ * The fill share is the largest tail of the work order whose estimated time
+ * on the fill CTAs (steps taken as proportional to 1/dx) stays within the
+ * teams' estimate, with no tube longer alone than that estimate.
+ * Errors: MXE_ESTATE (not an MXE_MIXED 1D context), MXE_ECUDA. */
+mxe_status mxe_batch_get_layout(mxe_ctx *ctx, int *teams, int *team_tubes, int *fill_ctas);
 
 /* ---- time-step history (2D grids) --------------------------------------- */
 

@@ -27,7 +27,7 @@ __all__ = [
     "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
     "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual", "mxe_set_adjoint_precision",
     "mxe_set_stage_occupancy", "mxe_set_source_scheme", "mxe_set_adjoint_limiter",
-    "mxe_set_face_packing",
+    "mxe_set_face_packing", "mxe_batch_get_layout",
 ]
 
 SOURCE_EXPLICIT, SOURCE_POINT_IMPLICIT = 0, 1
@@ -112,6 +112,7 @@ def lib():
             "mxe_batch_autotune": ([_P, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                     C.POINTER(C.c_double)], C.c_int),
             "mxe_batch_set_shape": ([_P, C.c_int, C.c_int], C.c_int),
+            "mxe_batch_get_layout": ([_P, _P, _P, _P], C.c_int),
             "mxe_set_dt_history": ([_P, C.c_longlong], C.c_int),
             "mxe_get_dt_history": ([_P, C.c_longlong, _P], C.c_int),
             "mxe_adjoint_record": ([_P, C.c_int, _P], C.c_int),
@@ -385,6 +386,12 @@ def mxe_batch_set_shape(ctx, nt, cl):
     _check(ctx, lib().mxe_batch_set_shape(ctx, nt, cl))
 
 
+def mxe_batch_get_layout(ctx):
+    teams, tubes, fill = C.c_int(), C.c_int(), C.c_int()
+    _check(ctx, lib().mxe_batch_get_layout(ctx, C.byref(teams), C.byref(tubes), C.byref(fill)))
+    return teams.value, tubes.value, fill.value
+
+
 # ------------------------------------------------------------ convenience
 _ENUM = {
     "fp64": FP64, "mixed": MIXED, "hll": FLUX_HLL, "rusanov": FLUX_RUSANOV,
@@ -546,3 +553,7 @@ class Batch(Solver):
 
     def set_shape(self, nt, cl):
         mxe_batch_set_shape(self.ctx, nt, cl)
+
+    def layout(self):
+        """(teams, tubes handed to the teams, CTAs of the fill launch)."""
+        return mxe_batch_get_layout(self.ctx)

@@ -101,7 +101,10 @@ struct mxe_ctx {
     TubeDesc* tdesc_d = nullptr;
     TubeClock* tclk = nullptr;
     int* order_d = nullptr;           // mixed tubes: hand-out order (longest work first)
-    int* queue_d = nullptr;           // mixed tubes: work counter
+    std::vector<int> order_h;         // the same order on the host
+    int* queue_d = nullptr;           // mixed tubes: work counters of the team and fill launches
+    cudaStream_t fill_stream = nullptr;    // the fill launch (forked from and joined to the work stream)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int tune_nt = 128, tune_cl = 1;   // block shape of the mixed tube launch
     bool tuned = false;
     int nsm = 0;
@@ -286,9 +289,13 @@ static mxe_status tubes_setup(mxe_ctx* c) {
     });
     CK(cudaMalloc(&c->order_d, sizeof(int) * n));
     CK(cudaMemcpy(c->order_d, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&c->queue_d, sizeof(int)));
-    CK(cudaMemset(c->queue_d, 0, sizeof(int)));
+    c->order_h = order;
+    CK(cudaMalloc(&c->queue_d, 2 * sizeof(int)));
+    CK(cudaMemset(c->queue_d, 0, 2 * sizeof(int)));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->fill_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -461,6 +468,9 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->adjF);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -869,12 +879,56 @@ static TubeMixedArgs tubes_mixed_args(mxe_ctx* c, int max_steps, double t_end) {
 
 // Launch shape of the persistent tube kernel with nt threads per CTA and
 // teams of cl CTAs (a cluster when cl > 1): as many teams as can be
-// resident at once, at most one per tube.
+// resident at once, at most one per tube.  Clusters are placed whole within
+// a GPU processing cluster, so a cluster launch can leave CTA slots unused
+// (on the GB300, 36 teams of 8 CTAs at two CTAs per SM occupy 144 of the 152
+// SMs).  Those slots run a second, concurrent launch of single CTAs ("fill")
+// that takes the smallest tubes, the tail of the work order: `nA` tubes go to
+// the teams, the rest to the fill CTAs.
 struct TubeLaunch {
     const void* kern;
     size_t smem;
     int nt, cl, teams;
+    int nA;              // tubes handed to the teams (order[0, nA))
+    int fill;            // single-CTA fill launch over order[nA, ntubes), 0 for none
 };
+
+// The fill launch's share: the largest tail of the work order whose estimated
+// time on the fill CTAs stays within the teams' estimated time, and no tube of
+// which would take longer alone.  Estimates in CTA passes over a chunk
+// (nt - 2 cells), steps taken as proportional to 1 / dx: a team spends
+// cl * ceil(chunks / cl) CTA passes on a step of a tube, one CTA `chunks`.
+static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L) {
+    const int n = c->ntubes;
+    L->nA = n;
+    if (L->fill <= 0 || n < 2) {
+        L->fill = 0;
+        return;
+    }
+    const int C = L->nt - 2;
+    std::vector<double> team(n), solo(n);
+    double TA = 0.0;
+    for (int q = 0; q < n; ++q) {
+        const TubeDesc& d = c->tdesc[c->order_h[q]];
+        const double steps = 1.0 / d.dx;
+        const int ch = (d.n + C - 1) / C;
+        team[q] = (double)((ch + L->cl - 1) / L->cl) * steps / L->teams;
+        solo[q] = (double)ch * steps;
+        TA += team[q];
+    }
+    double TB = 0.0;
+    int nA = n;
+    while (nA > 1) {
+        const int q = nA - 1;
+        const double ta = TA - team[q], tb = TB + solo[q] / L->fill;
+        if (tb > ta || solo[q] > ta) break;
+        TA = ta;
+        TB = tb;
+        nA = q;
+    }
+    L->nA = nA;
+    L->fill = nA < n ? std::min(L->fill, n - nA) : 0;
+}
 
 static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
     const bool pl = tubes_planar(c);
@@ -882,6 +936,8 @@ static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
     L->smem = tubes_mixed_smem(pl, nt);
     L->nt = nt;
     L->cl = cl;
+    int per = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, L->kern, nt, L->smem));
     int teams = 0;
     if (cl > 1) {
         cudaLaunchConfig_t lc = {};
@@ -897,38 +953,62 @@ static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
         lc.gridDim = dim3(cl * c->ntubes, 1, 1);
         CK(cudaOccupancyMaxActiveClusters(&teams, L->kern, &lc));
     } else {
-        int per = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, L->kern, nt, L->smem));
         teams = per * c->nsm;
     }
     if (teams < 1) return fail(c, MXE_ECUDA, "tube block shape %d x %d does not fit", nt, cl);
     L->teams = std::min(teams, c->ntubes);
+    L->fill = cl > 1 && teams < c->ntubes ? per * c->nsm - cl * teams : 0;
+    tube_fill_split(c, L);
+    L->teams = std::min(L->teams, L->nA);
     return MXE_OK;
 }
 
-// Queue reset + one persistent launch on `st` (no other runtime call, so it
-// can be captured into a graph).
-static mxe_status launch_tubes_mixed(mxe_ctx* c, cudaStream_t st, const TubeMixedArgs& a,
-                                     const TubeLaunch& L) {
+static cudaError_t launch_tube_grid(cudaStream_t st, const TubeLaunch& L, int cl, int nblocks,
+                                    const TubeMixedArgs& a, const ParamsT<float>& p,
+                                    const MixedPolicy& mp) {
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute at[1];
     lc.blockDim = dim3(L.nt, 1, 1);
-    lc.gridDim = dim3(L.cl * L.teams, 1, 1);
+    lc.gridDim = dim3(nblocks, 1, 1);
     lc.dynamicSmemBytes = L.smem;
     lc.stream = st;
-    if (L.cl > 1) {
+    if (cl > 1) {
         at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = L.cl;
+        at[0].val.clusterDim.x = cl;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
     }
-    ParamsT<float> p = fparams(c);
-    MixedPolicy mp = c->mp;
     void* args[] = {(void*)&a, (void*)&p, (void*)&mp};
-    CK(cudaMemsetAsync(c->queue_d, 0, sizeof(int), st));
-    CK(cudaLaunchKernelExC(&lc, L.kern, args));
+    return cudaLaunchKernelExC(&lc, L.kern, args);
+}
+
+// Queue reset + the persistent team launch on `st`, and the fill launch on
+// the fill stream, forked after the reset and joined back into `st` (runtime
+// calls that can be captured into a graph).  The two launches share no data
+// but their tubes' disjoint state and never wait on each other.
+static mxe_status launch_tubes_mixed(mxe_ctx* c, cudaStream_t st, const TubeMixedArgs& a,
+                                     const TubeLaunch& L) {
+    const ParamsT<float> p = fparams(c);
+    const MixedPolicy mp = c->mp;
+    CK(cudaMemsetAsync(c->queue_d, 0, 2 * sizeof(int), st));
+    if (L.fill > 0) {
+        CK(cudaEventRecord(c->ev_fork, st));
+        CK(cudaStreamWaitEvent(c->fill_stream, c->ev_fork, 0));
+    }
+    TubeMixedArgs aA = a;
+    aA.ntubes = L.nA;
+    CK(launch_tube_grid(st, L, L.cl, L.cl * L.teams, aA, p, mp));
+    if (L.fill > 0) {
+        TubeMixedArgs aB = a;
+        aB.order = a.order + L.nA;
+        aB.ntubes = a.ntubes - L.nA;
+        aB.queue = a.queue + 1;
+        CK(launch_tube_grid(c->fill_stream, L, 1, L.fill, aB, p, mp));
+        CK(cudaEventRecord(c->ev_join, c->fill_stream));
+        CK(cudaStreamWaitEvent(st, c->ev_join, 0));
+    }
     return MXE_OK;
 }
 
@@ -1253,6 +1333,19 @@ extern "C" mxe_status mxe_batch_autotune(mxe_ctx* c, double t_probe, int* nt_out
     if (nt_out) *nt_out = bnt;
     if (cl_out) *cl_out = bcl;
     if (ms_out) *ms_out = best;
+    return MXE_OK;
+}
+
+extern "C" mxe_status mxe_batch_get_layout(mxe_ctx* c, int* teams, int* team_tubes,
+                                           int* fill_ctas) {
+    if (!c) return MXE_EINVAL;
+    if (!c->tubes || !c->mixed) return fail(c, MXE_ESTATE, "layout of an MXE_MIXED 1D context only");
+    TubeLaunch L;
+    mxe_status s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L);
+    if (s != MXE_OK) return s;
+    if (teams) *teams = L.teams;
+    if (team_tubes) *team_tubes = L.nA;
+    if (fill_ctas) *fill_ctas = L.fill;
     return MXE_OK;
 }
 

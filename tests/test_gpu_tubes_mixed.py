@@ -103,6 +103,30 @@ def test_mixed_tubes_shape_invariance(mx):
             assert np.array_equal(st, ref[1]), shape
 
 
+def test_mixed_tubes_fill_launch(mx):
+    """More tubes than 8-CTA teams: the team launch leaves CTA slots unused
+    (clusters are placed whole), and a concurrent launch of single CTAs takes
+    the smallest tubes.  The layout shows both launches; the batch is
+    bitwise the single-CTA (128 x 1) batch, repeated runs replay the graph."""
+    tubes = wl.batch_tubes(64, nmin=100, nmax=3000)
+    b = sod_batch(mx, tubes, (256, 8))
+    teams, team_tubes, fill = b.layout()
+    print(f"layout 256 x 8: {teams} teams take {team_tubes} tubes, {fill} fill CTAs "
+          f"take {len(tubes) - team_tubes}")
+    assert fill > 0 and 0 < team_tubes < len(tubes) and teams <= team_tubes
+    b.run(10 ** 6, 0.01)
+    ref = sod_batch(mx, tubes, (128, 1))
+    assert ref.layout()[2] == 0
+    ref.run(10 ** 6, 0.01)
+    assert np.array_equal(b.get_moments("conserved"), ref.get_moments("conserved"))
+    t, st = b.clock()
+    tr, sr = ref.clock()
+    assert np.array_equal(st, sr) and np.allclose(t, 0.01, rtol=0, atol=1e-15)
+    b.run(10 ** 6, 0.02)                   # a new t_end: re-captured graph with both launches
+    ref.run(10 ** 6, 0.02)
+    assert np.array_equal(b.get_moments("conserved"), ref.get_moments("conserved"))
+
+
 def test_mixed_batch_equals_single_tubes(mx):
     """The work queue hands tubes out in any order: each tube of the batch is
     bitwise the tube run alone in its own context."""
