@@ -63,6 +63,8 @@ long long adj_f32_floats(const Grid2D& g);
 extern "C" __global__ void mxe_adj_pack(const double* dense, double* pitched, Grid2D g, int to_pitched,
                                         unsigned long long* nonfinite);
 size_t tubes_mixed_smem(bool planar, int nt);
+void tube_rates(bool planar, const double* U, const TubeDesc* tubes, int ntubes, float sl,
+                float kw, float* rates, cudaStream_t st);
 int tile_x();
 int tile_y();
 int tubes_threads();
@@ -105,6 +107,8 @@ struct mxe_ctx {
     int* queue_d = nullptr;           // mixed tubes: work counters of the team and fill launches
     cudaStream_t fill_stream = nullptr;    // the fill launch (forked from and joined to the work stream)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    float* rates_d = nullptr;         // per-tube CFL rate (step estimates of the split)
+    int lay_teams = 0, lay_nA = 0, lay_fill = 0;   // layout of the last mixed tube launch
     int tune_nt = 128, tune_cl = 1;   // block shape of the mixed tube launch
     bool tuned = false;
     int nsm = 0;
@@ -290,6 +294,7 @@ static mxe_status tubes_setup(mxe_ctx* c) {
     CK(cudaMalloc(&c->order_d, sizeof(int) * n));
     CK(cudaMemcpy(c->order_d, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     c->order_h = order;
+    CK(cudaMalloc(&c->rates_d, sizeof(float) * n));
     CK(cudaMalloc(&c->queue_d, 2 * sizeof(int)));
     CK(cudaMemset(c->queue_d, 0, 2 * sizeof(int)));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -457,6 +462,7 @@ extern "C" void mxe_destroy(mxe_ctx* c) {
     cudaFree(c->dts_d);
     cudaFree(c->order_d);
     cudaFree(c->queue_d);
+    cudaFree(c->rates_d);
     cudaFree(c->dth);
     cudaFree(c->tape);
     cudaFree(c->adjP);
@@ -893,15 +899,41 @@ struct TubeLaunch {
     int fill;            // single-CTA fill launch over order[nA, ntubes), 0 for none
 };
 
+// Estimated steps of every tube in a run (indexed by tube): the prescribed
+// count, or min(max_steps, (t_end - t) m / CFL) with m the CFL rate of the
+// tube's current state (one small kernel; synchronises the stream).
+static mxe_status tube_steps(mxe_ctx* c, int max_steps, double t_end, int n_fixed,
+                             std::vector<double>& steps) {
+    const int n = c->ntubes;
+    steps.assign(n, (double)(n_fixed > 0 ? n_fixed : max_steps));
+    if (n_fixed > 0) return MXE_OK;
+    std::vector<float> rate(n);
+    std::vector<TubeClock> ck(n);
+    tube_rates(tubes_planar(c), c->U, c->tdesc_d, n, (float)c->sp.sigma_lim, (float)c->sp.k_ws,
+               c->rates_d, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(rate.data(), c->rates_d, sizeof(float) * n, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(ck.data(), c->tclk, sizeof(TubeClock) * n, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < n; ++b) {
+        const double left = std::max(t_end - ck[b].t, 0.0) * (double)rate[b] / c->cfg.cfl;
+        if (std::isfinite(left)) steps[b] = std::min(steps[b], std::ceil(left));
+    }
+    return MXE_OK;
+}
+
 // The fill launch's share: the largest tail of the work order whose estimated
 // time on the fill CTAs stays within the teams' estimated time, and no tube of
 // which would take longer alone.  Estimates in CTA passes over a chunk
-// (nt - 2 cells), steps taken as proportional to 1 / dx: a team spends
+// (nt - 2 cells) times the tube's estimated steps: a team spends
 // cl * ceil(chunks / cl) CTA passes on a step of a tube, one CTA `chunks`.
-static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L) {
+// Without estimates (steps == NULL) there is no fill launch.
+static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L, const std::vector<double>* est) {
     const int n = c->ntubes;
     L->nA = n;
-    if (L->fill <= 0 || n < 2) {
+    if (L->fill <= 0 || n < 2 || !est) {
         L->fill = 0;
         return;
     }
@@ -910,7 +942,7 @@ static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L) {
     double TA = 0.0;
     for (int q = 0; q < n; ++q) {
         const TubeDesc& d = c->tdesc[c->order_h[q]];
-        const double steps = 1.0 / d.dx;
+        const double steps = (*est)[c->order_h[q]];
         const int ch = (d.n + C - 1) / C;
         team[q] = (double)((ch + L->cl - 1) / L->cl) * steps / L->teams;
         solo[q] = (double)ch * steps;
@@ -930,7 +962,8 @@ static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L) {
     L->fill = nA < n ? std::min(L->fill, n - nA) : 0;
 }
 
-static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
+static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L,
+                                    const std::vector<double>* est = nullptr) {
     const bool pl = tubes_planar(c);
     L->kern = tubes_mixed_kernel(pl, nt);
     L->smem = tubes_mixed_smem(pl, nt);
@@ -958,7 +991,7 @@ static mxe_status tube_launch_shape(mxe_ctx* c, int nt, int cl, TubeLaunch* L) {
     if (teams < 1) return fail(c, MXE_ECUDA, "tube block shape %d x %d does not fit", nt, cl);
     L->teams = std::min(teams, c->ntubes);
     L->fill = cl > 1 && teams < c->ntubes ? per * c->nsm - cl * teams : 0;
-    tube_fill_split(c, L);
+    tube_fill_split(c, L, est);
     L->teams = std::min(L->teams, L->nA);
     return MXE_OK;
 }
@@ -992,6 +1025,9 @@ static mxe_status launch_tubes_mixed(mxe_ctx* c, cudaStream_t st, const TubeMixe
                                      const TubeLaunch& L) {
     const ParamsT<float> p = fparams(c);
     const MixedPolicy mp = c->mp;
+    c->lay_teams = L.teams;
+    c->lay_nA = L.nA;
+    c->lay_fill = L.fill;
     CK(cudaMemsetAsync(c->queue_d, 0, 2 * sizeof(int), st));
     if (L.fill > 0) {
         CK(cudaEventRecord(c->ev_fork, st));
@@ -1018,10 +1054,12 @@ static mxe_status launch_tubes_mixed(mxe_ctx* c, cudaStream_t st, const TubeMixe
 static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const double* dts,
                                   int ndts) {
     TubeLaunch L;
-    mxe_status s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L);
-    if (s != MXE_OK) return s;
+    std::vector<double> est;
+    mxe_status s;
     if (dts) {                                   // prescribed steps: direct launch
-        s = upload_dts(c, dts, ndts);
+        s = tube_steps(c, ndts, INFINITY, ndts, est);
+        if (s == MXE_OK) s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L, &est);
+        if (s == MXE_OK) s = upload_dts(c, dts, ndts);
         if (s != MXE_OK) return s;
         TubeMixedArgs a = tubes_mixed_args(c, ndts, INFINITY);
         a.dt_fixed = c->dts_d;
@@ -1034,6 +1072,11 @@ static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
+        // the team / fill division of the captured launch, from the current
+        // state's step estimates
+        s = tube_steps(c, max_steps, t_end, 0, est);
+        if (s == MXE_OK) s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L, &est);
+        if (s != MXE_OK) return s;
         TubeMixedArgs a = tubes_mixed_args(c, max_steps, t_end);
         CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         s = launch_tubes_mixed(c, c->cap_stream, a, L);
@@ -1283,13 +1326,16 @@ extern "C" mxe_status mxe_batch_autotune(mxe_ctx* c, double t_probe, int* nt_out
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(Usave, c->U, sizeof(double) * c->nelem, cudaMemcpyDeviceToDevice,
                             c->stream);
+    std::vector<double> est;
+    if (e == cudaSuccess && tube_steps(c, 1 << 30, t0 + t_probe, 0, est) != MXE_OK)
+        e = cudaErrorUnknown;
     const int nts[2] = {128, 256}, cls[4] = {1, 2, 4, 8};
     float best = INFINITY;
     int bnt = c->tune_nt, bcl = c->tune_cl;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
         for (int j = 0; j < 4 && e == cudaSuccess; ++j) {
             TubeLaunch L;
-            if (tube_launch_shape(c, nts[i], cls[j], &L) != MXE_OK) {
+            if (tube_launch_shape(c, nts[i], cls[j], &L, &est) != MXE_OK) {
                 cudaGetLastError();
                 continue;                       // shape does not fit on this device
             }
@@ -1340,12 +1386,17 @@ extern "C" mxe_status mxe_batch_get_layout(mxe_ctx* c, int* teams, int* team_tub
                                            int* fill_ctas) {
     if (!c) return MXE_EINVAL;
     if (!c->tubes || !c->mixed) return fail(c, MXE_ESTATE, "layout of an MXE_MIXED 1D context only");
-    TubeLaunch L;
-    mxe_status s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L);
-    if (s != MXE_OK) return s;
-    if (teams) *teams = L.teams;
-    if (team_tubes) *team_tubes = L.nA;
-    if (fill_ctas) *fill_ctas = L.fill;
+    if (c->lay_nA == 0) {            // nothing launched yet: the teams alone
+        TubeLaunch L;
+        mxe_status s = tube_launch_shape(c, c->tune_nt, c->tune_cl, &L);
+        if (s != MXE_OK) return s;
+        c->lay_teams = L.teams;
+        c->lay_nA = L.nA;
+        c->lay_fill = L.fill;
+    }
+    if (teams) *teams = c->lay_teams;
+    if (team_tubes) *team_tubes = c->lay_nA;
+    if (fill_ctas) *fill_ctas = c->lay_fill;
     return MXE_OK;
 }
 
@@ -1356,6 +1407,7 @@ extern "C" mxe_status mxe_batch_set_shape(mxe_ctx* c, int nt, int cl) {
         return fail(c, MXE_EINVAL, "shape must be nt in {128, 256}, cl in {1, 2, 4, 8}");
     c->tune_nt = nt;
     c->tune_cl = cl;
+    c->lay_nA = 0;                   // the layout of the next launch is not known yet
     return MXE_OK;
 }
 

@@ -465,6 +465,58 @@ MXE_TUBES_MIXED(mxe_tubes14_mixed_planar_128, PhysPlanar, 128, 4)
 MXE_TUBES_MIXED(mxe_tubes14_mixed_planar_256, PhysPlanar, 256, 2)
 #undef MXE_TUBES_MIXED
 
+// CFL rate max_cells |lambda|_max / dx of every tube's current state (one
+// block per tube; the same FP64 primitive recovery and FP32 wave speeds as
+// the march), for the host's estimate of each tube's step count when it
+// divides the tubes between the team and fill launches.
+template <class PH>
+__device__ void tube_rates_body(const double* U, const TubeDesc* tubes, float sl, float kw,
+                                float* rates) {
+    constexpr int NF = PH::NF;
+    const TubeDesc td = tubes[blockIdx.x];
+    const double* Ut = U + td.off;
+    const float idx = (float)(1.0 / td.dx);
+    float r = 0.0f;
+    for (int i = threadIdx.x; i < td.n; i += blockDim.x) {
+        double Uc[NF], Q[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Uc[k] = Ut[(long long)PH::ufield(k) * td.n + i];
+        PH::cons2prim_fast(Uc, Q);
+        float Qf[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Qf[k] = (float)Q[k];
+        float ri = PH::rate_x(Qf, sl, kw) * idx;
+        if (!(ri >= 0.0f)) ri = __int_as_float(0x7f800000);
+        r = fmaxf(r, ri);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    __shared__ float wr[32];
+    if ((threadIdx.x & 31) == 0) wr[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, wr[w]);
+        rates[blockIdx.x] = r;
+    }
+}
+extern "C" __global__ void __launch_bounds__(256) mxe_tube_rates14(const double* U,
+                                                                  const TubeDesc* tubes, float sl,
+                                                                  float kw, float* rates) {
+    tube_rates_body<PhysGeneral>(U, tubes, sl, kw, rates);
+}
+extern "C" __global__ void __launch_bounds__(256) mxe_tube_rates14_planar(const double* U,
+                                                                         const TubeDesc* tubes,
+                                                                         float sl, float kw,
+                                                                         float* rates) {
+    tube_rates_body<PhysPlanar>(U, tubes, sl, kw, rates);
+}
+
+void tube_rates(bool planar, const double* U, const TubeDesc* tubes, int ntubes, float sl,
+                float kw, float* rates, cudaStream_t st) {
+    if (planar) mxe_tube_rates14_planar<<<ntubes, 256, 0, st>>>(U, tubes, sl, kw, rates);
+    else mxe_tube_rates14<<<ntubes, 256, 0, st>>>(U, tubes, sl, kw, rates);
+}
+
 // Kernel and dynamic shared memory of one block shape (nt = 128 or 256).
 const void* tubes_mixed_kernel(bool planar, int nt) {
     if (planar) return nt == 256 ? (const void*)mxe_tubes14_mixed_planar_256

@@ -106,15 +106,17 @@ def test_mixed_tubes_shape_invariance(mx):
 def test_mixed_tubes_fill_launch(mx):
     """More tubes than 8-CTA teams: the team launch leaves CTA slots unused
     (clusters are placed whole), and a concurrent launch of single CTAs takes
-    the smallest tubes.  The layout shows both launches; the batch is
-    bitwise the single-CTA (128 x 1) batch, repeated runs replay the graph."""
+    the smallest tubes (the division uses each tube's step estimate from
+    its current CFL rate).  The layout of the run shows both launches; the
+    batch is bitwise the single-CTA (128 x 1) batch, also after a graph
+    re-capture for a new t_end."""
     tubes = wl.batch_tubes(64, nmin=100, nmax=3000)
     b = sod_batch(mx, tubes, (256, 8))
+    b.run(10 ** 6, 0.01)
     teams, team_tubes, fill = b.layout()
     print(f"layout 256 x 8: {teams} teams take {team_tubes} tubes, {fill} fill CTAs "
           f"take {len(tubes) - team_tubes}")
     assert fill > 0 and 0 < team_tubes < len(tubes) and teams <= team_tubes
-    b.run(10 ** 6, 0.01)
     ref = sod_batch(mx, tubes, (128, 1))
     assert ref.layout()[2] == 0
     ref.run(10 ** 6, 0.01)
