@@ -266,8 +266,11 @@ mxe_status mxe_batch_get_clock(mxe_ctx *ctx, double *t, long long *steps);
  * queue ordered by expected work (largest first); when the teams cannot use
  * every CTA slot of the device (clusters are placed whole within a GPU
  * processing cluster), a second, concurrent launch of single CTAs takes the
- * smallest tubes (see mxe_batch_get_layout).  Results do not depend on which
- * launch, team or CTA advances a tube. */
+ * smallest tubes (see mxe_batch_get_layout).  Dividing the tubes estimates
+ * each tube's steps from its current CFL rate (a small kernel, and a
+ * synchronisation of the context stream, whenever the run's graph is
+ * captured: a new t_end, max_steps, block shape or launch argument).
+ * Results do not depend on which launch, team or CTA advances a tube. */
 mxe_status mxe_batch_run(mxe_ctx *ctx, int max_steps, double t_end);
 
 /* MXE_MIXED tube contexts: time every block shape (128 or 256 threads per
@@ -286,13 +289,17 @@ mxe_status mxe_batch_autotune(mxe_ctx *ctx, double t_probe, int *nt_out, int *cl
  * cl in {1, 2, 4, 8}); the default is 128 x 1. */
 mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
 
-/* MXE_MIXED tube contexts: the launch layout mxe_batch_run uses with the
- * current block shape (outputs may be NULL): teams of the team launch, the
- * tubes handed to it (the largest, in work order), and the CTAs of the fill
- * launch of single CTAs that takes the remaining tubes (0: no fill launch).
+/* MXE_MIXED tube contexts: the launch layout of the last mxe_batch_run (or
+ * autotuner candidate); before the first run, or after mxe_batch_set_shape,
+ * that of the team launch alone.  Outputs (may be NULL): teams of the team
+ * launch, the tubes handed to it (the largest, in work order), and the CTAs
+ * of the fill launch of single CTAs that takes the remaining tubes (0: no
+ * fill launch).
  * The fill share is the largest tail of the work order whose estimated time
- * on the fill CTAs (steps taken as proportional to 1/dx) stays within the
- * teams' estimate, with no tube longer alone than that estimate.
+ * on the fill CTAs stays within the teams' estimate, with no tube longer
+ * alone than that estimate; a tube's estimate is CTA passes over a chunk
+ * times its steps in the run, min(max_steps, (t_end - t) m / CFL) with m the
+ * CFL rate of its current state (prescribed steps count as given).
  * Errors: MXE_ESTATE (not an MXE_MIXED 1D context), MXE_ECUDA. */
 mxe_status mxe_batch_get_layout(mxe_ctx *ctx, int *teams, int *team_tubes, int *fill_ctas);
 
