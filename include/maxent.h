@@ -289,8 +289,8 @@ mxe_status mxe_batch_autotune(mxe_ctx *ctx, double t_probe, int *nt_out, int *cl
  * cl in {1, 2, 4, 8}); the default is 128 x 1. */
 mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
 
-/* MXE_MIXED tube contexts: the launch layout of the last mxe_batch_run (or
- * autotuner candidate); before the first run, or after mxe_batch_set_shape,
+/* MXE_MIXED tube contexts: the launch layout of the last mxe_batch_run;
+ * before the first run, or after mxe_batch_set_shape or mxe_batch_autotune,
  * that of the team launch alone.  Outputs (may be NULL): teams of the team
  * launch, the tubes handed to it (the largest, in work order), and the CTAs
  * of the fill launch of single CTAs that takes the remaining tubes (0: no

@@ -1376,6 +1376,7 @@ extern "C" mxe_status mxe_batch_autotune(mxe_ctx* c, double t_probe, int* nt_out
     c->tune_nt = bnt;
     c->tune_cl = bcl;
     c->tuned = true;
+    c->lay_nA = 0;                   // the layout of the next launch is not known yet
     if (nt_out) *nt_out = bnt;
     if (cl_out) *cl_out = bcl;
     if (ms_out) *ms_out = best;
