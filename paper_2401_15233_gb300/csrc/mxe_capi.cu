@@ -109,6 +109,7 @@ struct mxe_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float* rates_d = nullptr;         // per-tube CFL rate (step estimates of the split)
     int lay_teams = 0, lay_nA = 0, lay_fill = 0;   // layout of the last mixed tube launch
+    int g_lay_teams = 0, g_lay_nA = 0, g_lay_fill = 0;   // layout captured in the graph
     int tune_nt = 128, tune_cl = 1;   // block shape of the mixed tube launch
     bool tuned = false;
     int nsm = 0;
@@ -1099,8 +1100,14 @@ static mxe_status run_tubes_mixed(mxe_ctx* c, int max_steps, double t_end, const
         c->g_cl = c->tune_cl;
         c->g_gen = c->gen;
         c->g_planar = tubes_planar(c);
+        c->g_lay_teams = c->lay_teams;
+        c->g_lay_nA = c->lay_nA;
+        c->g_lay_fill = c->lay_fill;
     }
     CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->lay_teams = c->g_lay_teams;
+    c->lay_nA = c->g_lay_nA;
+    c->lay_fill = c->g_lay_fill;
     return MXE_OK;
 }
 
