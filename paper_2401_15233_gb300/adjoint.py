@@ -154,12 +154,19 @@ def forward_checkpointed(prob: JetsProblem, p):
         U = torch.empty((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
         s.get_moments("conserved", out=U)
         return float(prob.probe_of(U)), [], dts, s
+    # checkpoints every ckpt steps; the last segment is recorded into the
+    # one-segment tape as it is marched, so the backward starts on it without
+    # a replay
     ckpts = []
-    for _ in range(prob.nsteps // prob.ckpt):
+    nseg = prob.nsteps // prob.ckpt
+    for k in range(nseg):
         U = torch.empty((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
         s.get_moments("conserved", out=U)
         ckpts.append(U)
-        s.step(prob.ckpt, float("inf"), sync=False)
+        if k == nseg - 1:
+            s.adjoint_record(None, prob.ckpt)
+        else:
+            s.step(prob.ckpt, float("inf"), sync=False)
     dts = s.dt_history(prob.nsteps)
     U = torch.empty((14, prob.n, prob.n), dtype=torch.float64, device="cuda")
     s.get_moments("conserved", out=U)
@@ -168,7 +175,8 @@ def forward_checkpointed(prob: JetsProblem, p):
 
 def backward_checkpointed(prob: JetsProblem, s: Solver, ckpts, dts, gJ=1.0):
     """dJ/dp by the reverse sweep, segment by segment (recomputing each
-    segment from its checkpoint).  With the FP32 face-state reverse, a
+    segment from its checkpoint, except the last, which the forward left on
+    the tape).  With the FP32 face-state reverse, a
     segment whose adjoint leaves the FP32 range (non-finite values) is swept
     again with the FP64 reverse from the same incoming adjoint; the number of
     such segments is left in prob.fp64_fallbacks."""
@@ -185,7 +193,7 @@ def backward_checkpointed(prob: JetsProblem, s: Solver, ckpts, dts, gJ=1.0):
     # checkpointed segment, last first
     segments = [None] if getattr(prob, "tape_kept", False) else range(len(ckpts) - 1, -1, -1)
     for k in segments:
-        if k is not None:
+        if k is not None and k != len(ckpts) - 1:     # the last one is on the tape
             s.set_state(ckpts[k], kind="restore")
             s.adjoint_record(dts[k * prob.ckpt:(k + 1) * prob.ckpt])
         keep = ubar.clone() if mixed else None
