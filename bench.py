@@ -86,7 +86,7 @@ def parse():
     p.add_argument("--no-dt-history", action="store_true",
                    help="skip the crossing collisionless jets step-size history (1200^2, 10000 steps)")
     p.add_argument("--cpu-full", action="store_true",
-                   help="CPU baseline: also config 2 to t = 0.2 and config 3 at 1024^2 for 20 steps")
+                   help="CPU baseline: also the 4096-cell 14-moment Sod tube to t = 0.2 and the crossed jets at 1024^2 for 20 steps")
     p.add_argument("--only", default=None, choices=["batch", "adjoint", "cpu", "l1", "dt"],
                    help="run one secondary leg alone (profiling runs)")
     p.add_argument("--batch-t-end", type=float, default=0.2)
@@ -310,12 +310,12 @@ def _timed_steps(oracle, cfg, U, omp, seconds, max_steps):
 def cpu_baseline(wl, full=False):
     """The FP64 oracle as it stands on the host cores: single-threaded (the
     paper's 1-core basis) and its OpenMP build on all cores (bitwise the
-    same arithmetic), on bounded samples of the benchmark configurations:
-    config 3 (crossed jets, RK2, MUSCL, HLL) on a 128^2 grid, config 1
-    (5-moment Sod, 1000 cells, first order, forward Euler) to t = 0.2 in full,
-    config 2 (14-moment Sod, 4096 cells, RK2, Kn = 0.01) over its first 100
-    steps.  full: also config 2 to t = 0.2 and config 3 at 1024^2 for 20
-    steps (minutes of CPU time).  Rate = cell-updates/s."""
+    same arithmetic), on bounded samples of the benchmark workloads: the
+    crossed jets (RK2, MUSCL, HLL) on a 128^2 grid, the 5-moment Sod tube
+    (1000 cells, first order, forward Euler) to t = 0.2 in full, the 14-moment
+    Sod tube (4096 cells, RK2, Kn = 0.01) over its first 100 steps.  full: also
+    the 14-moment tube to t = 0.2 and the crossed jets at 1024^2 for 20 steps
+    (minutes of CPU time).  Rate = cell-updates/s."""
     import oracle
     oracle.build()
     oracle.build(omp=True)
@@ -351,13 +351,13 @@ def cpu_baseline(wl, full=False):
             return len(hist), time.perf_counter() - t0
         return run
 
-    leg("config3_jets_128", 128 * 128, c3(128, 8.0, 200))
-    leg("config1_sod5_1000_to_t0.2", 1000, sod(5, 1000, 1, oracle.FE, 0.2, 10 ** 6))
-    leg("config2_sod14_4096_100_steps", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 100))
+    leg("jets_128", 128 * 128, c3(128, 8.0, 200))
+    leg("sod5_1000_to_t0.2", 1000, sod(5, 1000, 1, oracle.FE, 0.2, 10 ** 6))
+    leg("sod14_4096_100_steps", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 100))
     if full:
-        leg("config2_sod14_4096_to_t0.2", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 10 ** 7))
-        leg("config3_jets_1024_20_steps", 1024 * 1024, c3(1024, 1e9, 20))
-    h = out["config3_jets_128"]["all_core"]
+        leg("sod14_4096_to_t0.2", 4096, sod(14, 4096, 2, oracle.RK2, 0.2, 10 ** 7))
+        leg("jets_1024_20_steps", 1024 * 1024, c3(1024, 1e9, 20))
+    h = out["jets_128"]["all_core"]
     out["value"] = h["value"]
     out["cores"] = threads
     out["sample"] = (f"128x128 crossed jets (the benchmark workload's set-up), {h['steps']} RK2 "
@@ -769,7 +769,7 @@ def main():
 
     n = args.n
     setup = wl.jets_setup(Kn=0.1)
-    # the run of config 3: background at rest, jets entering through the slots
+    # the crossed-jets run: background at rest, jets entering through the slots
     # (the timed steps follow args.prerun untimed ones); the synthetic
     # developed state (a filled domain) is timed beside it
     rest = np.ascontiguousarray(np.moveaxis(wl.jets_initial(n, n, setup), -1, 0))

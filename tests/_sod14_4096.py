@@ -1,6 +1,6 @@
-"""Oracle trajectories of config 2 (the 4096-cell 14-moment Sod tube at five
+"""Oracle trajectories of the 4096-cell 14-moment Sod tube (at five
 Knudsen numbers, RK2, MUSCL, minmod, HLL, CFL 0.5, to t = 0.2) for
-tests/test_gpu_zconfig2.py.  They take minutes of CPU time, so conftest
+tests/test_gpu_zsod14_4096.py.  They take minutes of CPU time, so conftest
 starts them in a spawn-started process pool (OpenMP oracle, threads shared
 out by the expected step counts) as soon as that test is collected, and the
 rest of the GPU suite runs meanwhile.  Each run returns the final state, the

@@ -20,27 +20,28 @@ def orc():
     return oracle
 
 
-# Config 2's oracle trajectories take minutes: when its test is collected,
-# start them in a spawn-started process pool right away (no GPU work is done
-# in the workers), so that they run while the rest of the suite does.
-_CONFIG2 = {}
+# The 4096-cell 14-moment Sod tube's oracle trajectories take minutes: when
+# its test is collected, start them in a spawn-started process pool right
+# away (no GPU work is done in the workers), so that they run while the rest
+# of the suite does.
+_SOD4096 = {}
 
 
 def pytest_collection_finish(session):
-    if any("test_gpu_zconfig2" in it.nodeid for it in session.items):
-        from tests._config2 import Runs
-        _CONFIG2["runs"] = Runs()
+    if any("test_gpu_zsod14_4096" in it.nodeid for it in session.items):
+        from tests._sod14_4096 import Runs
+        _SOD4096["runs"] = Runs()
 
 
 def pytest_sessionfinish(session, exitstatus):
-    runs = _CONFIG2.pop("runs", None)
+    runs = _SOD4096.pop("runs", None)
     if runs is not None:
         runs.close()
 
 
 @pytest.fixture(scope="session")
-def config2_runs():
-    if "runs" not in _CONFIG2:
-        from tests._config2 import Runs
-        _CONFIG2["runs"] = Runs()
-    return _CONFIG2["runs"]
+def sod14_4096_runs():
+    if "runs" not in _SOD4096:
+        from tests._sod14_4096 import Runs
+        _SOD4096["runs"] = Runs()
+    return _SOD4096["runs"]

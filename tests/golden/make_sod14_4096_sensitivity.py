@@ -1,4 +1,4 @@
-"""Writes config2_sensitivity.txt: the data sensitivity of the 4096-cell
+"""Writes sod14_4096_sensitivity.txt: the data sensitivity of the 4096-cell
 14-moment Sod tube (RK2, MUSCL, minmod, HLL, CFL 0.5, hard-sphere BGK) at
 t = 0.2 for Kn in {1e-3, 1e-2, 0.1, 1, 10}, computed by the FP64 oracle
 alone: the relative L1 change of the density, the temperature
@@ -6,7 +6,7 @@ T = tr P / (3 rho) and the heat flux q_x when every primitive of the initial
 state is perturbed by 1e-7 relative (random signs, seeded per Kn).  Ten
 times these values is the bound of the mixed-precision path's L1 error
 against the oracle (the mixed-precision accuracy reading).  Run from the
-repository root:  python tests/golden/make_config2_sensitivity.py
+repository root:  python tests/golden/make_sod14_4096_sensitivity.py
 (about twenty minutes on eight cores)."""
 import os
 import sys
@@ -54,13 +54,13 @@ def main():
     threads = max(1, (os.cpu_count() or 5) // len(KNS))
     with ProcessPoolExecutor(len(KNS), mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(run, [(kn, threads) for kn in KNS]))
-    lines = ["# Data sensitivity of config 2 (14-moment Sod, 4096 cells, RK2 MUSCL minmod HLL,",
+    lines = ["# Data sensitivity of the 14-moment Sod tube ( 4096 cells, RK2 MUSCL minmod HLL,",
              "# CFL 0.5, hard-sphere BGK, t = 0.2), FP64 oracle: relative L1 change of rho, T, q_x",
              "# under a 1e-7 relative perturbation of every initial primitive.",
-             "# Written by make_config2_sensitivity.py (oracle only).  key = rho T q_x  (steps)"]
+             "# Written by make_sod14_4096_sensitivity.py (oracle only).  key = rho T q_x  (steps)"]
     for kn, l1, na, nb in res:
         lines.append(f"Kn{kn:g} = {l1[0]:.6e} {l1[1]:.6e} {l1[2]:.6e}  # {na} / {nb} steps")
-    with open(os.path.join(HERE, "config2_sensitivity.txt"), "w") as f:
+    with open(os.path.join(HERE, "sod14_4096_sensitivity.txt"), "w") as f:
         f.write("\n".join(lines) + "\n")
     print("\n".join(lines))
 

@@ -29,7 +29,7 @@ def gpu_cons(s):
     return soa_to_aos(s.get_moments("conserved"))
 
 
-# ------------------------------------------------------------------ 1D, 5-moment (config 1)
+# ------------------------------------------------------------------ 1D, 5-moment Sod, 1000 cells
 def sod5_pair(mx, orc, nx, Kn, order=1, integ="fe", flux="hll"):
     prim = wl.sod_prim(5, nx)
     s = mx.Solver(system=5, nx=nx, ny=1, order=order, integrator=integ, flux=flux)
@@ -90,8 +90,8 @@ def free_run_drift(mx, s, orc, cfg, U, nsteps, t_end):
     return first, field_rel_err(gpu_cons(s), U), tg, t
 
 
-def test_sod5_config1_per_step_parity(mx, orc):
-    """Config 1 (1000 cells, Kn = 0.01, first-order HLL, forward Euler): every
+def test_sod5_1000_per_step_parity(mx, orc):
+    """The 5-moment Sod tube (1000 cells, Kn = 0.01, first-order HLL, forward Euler): every
     step of the first 400 and every 50th step up to t = 0.2 from the oracle's
     state matches the oracle's next state to 1e-12."""
     s, cfg, U = sod5_pair(mx, orc, 1000, 0.01)
@@ -100,8 +100,8 @@ def test_sod5_config1_per_step_parity(mx, orc):
     print("config-1 per-step worst", max(worst, worst2))
 
 
-def test_sod5_config1_to_t02(mx, orc):
-    """Config 1 marched to t = 0.2 on each side's own clock (about 1.4e4
+def test_sod5_1000_to_t02(mx, orc):
+    """The 5-moment Sod tube marched to t = 0.2 on each side's own clock (about 1.4e4
     steps): both reach t_end, stay realizable, and agree in L1 to the bound
     below; the first divergent step is reported."""
     s, cfg, U = sod5_pair(mx, orc, 1000, 0.01)
@@ -116,7 +116,7 @@ def test_sod5_config1_to_t02(mx, orc):
     assert l1.max() <= 5e-2
 
 
-# ------------------------------------------------------------------ 1D, 14-moment (config 2)
+# ------------------------------------------------------------------ 1D, 14-moment Sod
 @pytest.mark.parametrize("Kn", [1e-3, 1e-2, 0.1, 1.0, 10.0])
 def test_sod14_1d_parity(mx, orc, Kn):
     nx = 256
@@ -175,7 +175,7 @@ def test_jets2d_one_step_general_state(mx, orc, nx, ny):
 
 
 def test_jets2d_trajectory_from_rest(mx, orc):
-    """Config 3 geometry from the uniform background, 24 steps at 48^2."""
+    """The crossed-jets geometry from the uniform background, 24 steps at 48^2."""
     n = 48
     setup = wl.jets_setup(Kn=0.1)
     prim = wl.jets_initial(n, n, setup)

@@ -1,4 +1,4 @@
-"""Config 2 at its stated size: the 1D-space 14-moment Sod tube, 4096 cells,
+"""The 1D-space 14-moment Sod tube at its stated size, 4096 cells,
 left rho = 1, P = 1 / right rho = 0.125, P = 0.1 (Maxwellians), RK2, MUSCL,
 minmod, HLL, CFL 0.5, hard-sphere BGK at Kn in {1e-3, 1e-2, 0.1, 1, 10}, to
 t = 0.2 (Sec. 4), against the FP64 oracle.
@@ -8,7 +8,7 @@ t = 0.2 (Sec. 4), against the FP64 oracle.
 - Mixed path: a free run to t = 0.2 on its own CFL clock; the relative L1
   error of the density, temperature and heat flux q_x against the oracle's
   run within 10x the oracle's own change under a 1e-7 data perturbation
-  (tests/golden/config2_sensitivity.txt, written by the oracle alone).
+  (tests/golden/sod14_4096_sensitivity.txt, written by the oracle alone).
   Measured inside the bound on every field for Kn <= 1 (0.1x to 0.35x of
   it); at Kn = 10 the temperature and heat flux are inside and the density
   is 1.05x the bound (3.77e-5 against 3.58e-5): recorded as an expected
@@ -34,7 +34,7 @@ KNS = (1e-3, 1e-2, 0.1, 1.0, 10.0)
 
 def sensitivity():
     out = {}
-    path = os.path.join(os.path.dirname(__file__), "golden", "config2_sensitivity.txt")
+    path = os.path.join(os.path.dirname(__file__), "golden", "sod14_4096_sensitivity.txt")
     for line in open(path):
         line = line.split("#")[0].strip()
         if "=" in line:
@@ -77,11 +77,11 @@ def fp64_per_step(mx, kn, r):
 
 
 @pytest.mark.parametrize("kn", KNS)
-def test_config2_fp64_per_step_along_oracle(mx, orc, config2_runs, kn):
-    r = config2_runs.get(kn)
+def test_sod14_4096_fp64_per_step_along_oracle(mx, orc, sod14_4096_runs, kn):
+    r = sod14_4096_runs.get(kn)
     assert r["t"] == pytest.approx(0.2, rel=1e-12)
     worst = fp64_per_step(mx, kn, r)
-    print(f"config 2, Kn {kn:g}: oracle {r['steps']} steps; FP64 per-step worst {worst:.1e} "
+    print(f"Sod 4096, Kn {kn:g}: oracle {r['steps']} steps; FP64 per-step worst {worst:.1e} "
           f"at steps {sorted(r['samples'])}")
 
 
@@ -92,7 +92,7 @@ MIXED_KNS = [pytest.param(kn, marks=pytest.mark.xfail(
 
 
 @pytest.mark.parametrize("kn", MIXED_KNS)
-def test_config2_mixed_l1_at_t02(mx, orc, config2_runs, kn):
+def test_sod14_4096_mixed_l1_at_t02(mx, orc, sod14_4096_runs, kn):
     nx = 4096
     sens = sensitivity()[kn]
     prim = aos_to_soa(wl.sod_prim(14, nx)[None])
@@ -102,10 +102,10 @@ def test_config2_mixed_l1_at_t02(mx, orc, config2_runs, kn):
     t_m, n_m = m.step(10 ** 7, 0.2)
     assert t_m == pytest.approx(0.2, rel=1e-12)
     Gm = soa_to_aos(m.get_moments("conserved"))
-    r = config2_runs.get(kn)
+    r = sod14_4096_runs.get(kn)
     l1 = np.array([np.abs(g - o).sum() / np.abs(o).sum()
                    for g, o in zip(rho_T_qx(Gm), rho_T_qx(r["U"]))])
     bound = 10 * sens
-    print(f"config 2, Kn {kn:g}: mixed {n_m} steps (oracle {r['steps']}); mixed L1 rho/T/q_x "
+    print(f"Sod 4096, Kn {kn:g}: mixed {n_m} steps (oracle {r['steps']}); mixed L1 rho/T/q_x "
           f"{l1[0]:.2e}/{l1[1]:.2e}/{l1[2]:.2e} (bound {bound[0]:.2e}/{bound[1]:.2e}/{bound[2]:.2e})")
     assert np.all(l1 <= bound), (kn, l1, bound)

@@ -307,7 +307,7 @@ def test_window_steps_periodic_and_1d(orc):
 
 # ------------------------------------------------------------------ realizability
 def test_c1_sod5_stays_realizable(orc):
-    """Config 1 (5-moment Sod, 1000 cells, Kn = 0.01, first-order HLL, FE,
+    """The 5-moment Sod tube (1000 cells, Kn = 0.01, first-order HLL, FE,
     CFL 0.5, t = 0.2): every cell ends with rho > 0, P > 0, sigma <= 1."""
     nx = 1000
     U = cons_field(orc, wl.sod_prim(5, nx)[None])
