@@ -280,12 +280,13 @@ def cpu_info():
     return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
 
 
-def _jets_oracle(oracle, wl, n):
+def _jets_oracle(oracle, wl, n, rest=False):
     """The crossed-jets workload on an n x n grid for the oracle: its
-    configuration and the developed state (conserved, (n, n, 14))."""
+    configuration and the developed state, or (rest) the background at rest
+    the run starts from (conserved, (n, n, 14))."""
     import numpy as np
     setup = wl.jets_setup(Kn=0.1)
-    prim = wl.jets_like_field(n, n, setup)
+    prim = wl.jets_initial(n, n, setup) if rest else wl.jets_like_field(n, n, setup)
     U = oracle.prim2cons_field(prim)
     lo, hi = setup["slot"]
     sides = [{"type": 0, "spans": [(lo, hi, setup["left"])]}, {"type": 0},
@@ -691,10 +692,11 @@ def bench_adjoint(world, n=512, nsteps=500, ckpt=50, only_precision=None):
     return out
 
 
-def workload_config(n, precision, world, planar=True, prerun=0):
-    """The benchmark's workload, as named in both arms' JSON lines."""
+def workload_config(n, world, planar=True, prerun=0):
+    """The benchmark's workload, as named in both arms' JSON lines (the
+    arithmetic each arm computes in is its `dtype`)."""
     return {"workload": f"crossed supersonic jets, 14-moment 2D RK2, {n}x{n}",
-            "n": n, "precision": precision, "flux": "hll", "limiter": "minmod",
+            "n": n, "flux": "hll", "limiter": "minmod",
             "Kn": 0.1, "mach": 3, "parallelism": f"replicas{world}", "planar": planar,
             "initial": f"background at rest, jets from the slots; timed after {prerun} untimed steps",
             "l2": "inputs larger than L2 (1.9 GB per state buffer), no flush"}
@@ -704,7 +706,8 @@ def run_reference(args, wl):
     """The reference arm: the FP64 oracle on the host cores (its OpenMP
     build, bitwise the arithmetic of the single-threaded oracle), each step
     one RK2 step (CFL included) of a bounded 96^2 sample of the crossed-jets
-    workload, rank 0 only."""
+    workload, run like the GPU arm's: from the background at rest, timed
+    after the same number of untimed steps; rank 0 only."""
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
         return
@@ -712,8 +715,8 @@ def run_reference(args, wl):
     oracle.build(omp=True)
     threads = oracle.threads(omp=True)
     n = 96
-    cfg, U = _jets_oracle(oracle, wl, n)
-    for _ in range(args.warmup):
+    cfg, U = _jets_oracle(oracle, wl, n, rest=True)
+    for _ in range(args.prerun + args.warmup):
         U = oracle.step(cfg, U, oracle.dt(cfg, U, 0.0, 10.0, omp=True), omp=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -722,13 +725,14 @@ def run_reference(args, wl):
     v = n * n * args.steps / el
     info = cpu_info()
     sample = (f"{n}x{n} crossed jets per step (bounded sample of the {args.n}^2 workload), "
+              f"from rest, timed after {args.prerun + args.warmup} untimed steps, "
               f"OpenMP oracle on {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args.n, "fp64 (oracle)", args.gpus),
+        "config": workload_config(args.n, args.gpus, True, args.prerun),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, **info},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -886,7 +890,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 (+f64 accumulator, f64 closure islands)",
         "data": "synthetic",
-        "config": workload_config(n, args.precision, world, planar, args.prerun),
+        "config": workload_config(n, world, planar, args.prerun),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": traffic * ncell if traffic else None,
