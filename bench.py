@@ -363,7 +363,7 @@ def cpu_baseline(wl, full=False):
     out["cores"] = threads
     out["sample"] = (f"128x128 crossed jets (the benchmark workload's set-up), {h['steps']} RK2 "
                      f"steps incl. CFL, {h['seconds']:.1f} s, OpenMP build on {threads} threads; "
-                     f"single-thread and configs 1-2 beside it")
+                     f"single-thread and the Sod tubes beside it")
     return out
 
 
