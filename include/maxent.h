@@ -303,6 +303,17 @@ mxe_status mxe_batch_set_shape(mxe_ctx *ctx, int nt, int cl);
  * Errors: MXE_ESTATE (not an MXE_MIXED 1D context), MXE_ECUDA. */
 mxe_status mxe_batch_get_layout(mxe_ctx *ctx, int *teams, int *team_tubes, int *fill_ctas);
 
+/* The division mxe_batch_run makes, as a host-only computation (no context,
+ * no device): n tubes in work order (largest first) with cells[q] cells and
+ * an estimated steps[q] steps in the run, chunks of `chunk` cells per CTA
+ * pass, `teams` teams of cl CTAs and `fill` single fill CTAs.  Output: the
+ * number of leading tubes for the teams (the rest go to the fill CTAs; n when
+ * fill is 0) and the estimated run time in CTA-pass units (may be NULL).
+ * MXE_EINVAL for n < 1, a NULL array, chunk, cl or teams < 1, fill < 0, a tube
+ * of < 1 cell or a negative or non-finite step estimate. */
+mxe_status mxe_batch_plan_fill(int n, const int *cells, const double *steps, int chunk, int cl,
+                               int teams, int fill, int *team_tubes, double *est_time);
+
 /* ---- time-step history (2D grids) --------------------------------------- */
 
 /* Keep the dt of every step in a device buffer of `capacity` entries

@@ -27,7 +27,7 @@ __all__ = [
     "mxe_batch_autotune", "mxe_batch_set_shape", "mxe_set_dt_history", "mxe_get_dt_history",
     "mxe_adjoint_record", "mxe_adjoint_run", "mxe_adjoint_residual", "mxe_set_adjoint_precision",
     "mxe_set_stage_occupancy", "mxe_set_source_scheme", "mxe_set_adjoint_limiter",
-    "mxe_set_face_packing", "mxe_batch_get_layout",
+    "mxe_set_face_packing", "mxe_batch_get_layout", "mxe_batch_plan_fill",
 ]
 
 SOURCE_EXPLICIT, SOURCE_POINT_IMPLICIT = 0, 1
@@ -113,6 +113,8 @@ def lib():
                                     C.POINTER(C.c_double)], C.c_int),
             "mxe_batch_set_shape": ([_P, C.c_int, C.c_int], C.c_int),
             "mxe_batch_get_layout": ([_P, _P, _P, _P], C.c_int),
+            "mxe_batch_plan_fill": ([C.c_int, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P,
+                                     _P], C.c_int),
             "mxe_set_dt_history": ([_P, C.c_longlong], C.c_int),
             "mxe_get_dt_history": ([_P, C.c_longlong, _P], C.c_int),
             "mxe_adjoint_record": ([_P, C.c_int, _P], C.c_int),
@@ -384,6 +386,20 @@ def mxe_batch_autotune(ctx, t_probe):
 
 def mxe_batch_set_shape(ctx, nt, cl):
     _check(ctx, lib().mxe_batch_set_shape(ctx, nt, cl))
+
+
+def mxe_batch_plan_fill(cells, steps, chunk, cl, teams, fill):
+    """Host-only: (tubes for the teams, estimated time) for tubes in work order."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    steps = np.ascontiguousarray(steps, dtype=np.float64)
+    if cells.shape != steps.shape or cells.ndim != 1:
+        raise ValueError("cells and steps must be 1-D arrays of the same length")
+    nA, t = C.c_int(), C.c_double()
+    st = lib().mxe_batch_plan_fill(len(cells), cells.ctypes.data, steps.ctypes.data, chunk, cl,
+                                   teams, fill, C.byref(nA), C.byref(t))
+    if st != OK:
+        raise MaxentError(st, "mxe_batch_plan_fill: invalid arguments")
+    return nA.value, t.value
 
 
 def mxe_batch_get_layout(ctx):

@@ -927,10 +927,50 @@ static mxe_status tube_steps(mxe_ctx* c, int max_steps, double t_end, int n_fixe
 
 // The fill launch's share: the largest tail of the work order whose estimated
 // time on the fill CTAs stays within the teams' estimated time, and no tube of
-// which would take longer alone.  Estimates in CTA passes over a chunk
-// (nt - 2 cells) times the tube's estimated steps: a team spends
-// cl * ceil(chunks / cl) CTA passes on a step of a tube, one CTA `chunks`.
-// Without estimates (steps == NULL) there is no fill launch.
+// which would take longer alone.  Tubes in work order (cells[q], steps[q]);
+// estimates in CTA passes over a chunk of C cells times the tube's steps: a
+// team of cl CTAs spends cl * ceil(chunks / cl) CTA passes on a step, one CTA
+// `chunks`.  Returns the number of tubes for the teams (the rest go to the
+// fill CTAs) and the estimated time of the run, max(teams, fill).
+static int plan_fill(int n, const int* cells, const double* steps, int C, int cl, int teams,
+                     int fill, double* time_out) {
+    std::vector<double> team(n), solo(n);
+    double TA = 0.0;
+    for (int q = 0; q < n; ++q) {
+        const int ch = (cells[q] + C - 1) / C;
+        team[q] = (double)((ch + cl - 1) / cl) * steps[q] / teams;
+        solo[q] = (double)ch * steps[q];
+        TA += team[q];
+    }
+    double TB = 0.0;
+    int nA = n;
+    while (fill > 0 && nA > 1) {
+        const int q = nA - 1;
+        const double ta = TA - team[q], tb = TB + solo[q] / fill;
+        if (tb > ta || solo[q] > ta) break;
+        TA = ta;
+        TB = tb;
+        nA = q;
+    }
+    if (time_out) *time_out = std::max(TA, TB);
+    return nA;
+}
+
+extern "C" mxe_status mxe_batch_plan_fill(int n, const int* cells, const double* steps,
+                                          int chunk, int cl, int teams, int fill, int* team_tubes,
+                                          double* est_time) {
+    if (n < 1 || !cells || !steps || chunk < 1 || cl < 1 || teams < 1 || fill < 0)
+        return MXE_EINVAL;
+    for (int q = 0; q < n; ++q)
+        if (cells[q] < 1 || !(steps[q] >= 0.0) || !std::isfinite(steps[q])) return MXE_EINVAL;
+    const int nA = plan_fill(n, cells, steps, chunk, cl, teams, fill, est_time);
+    if (team_tubes) *team_tubes = nA;
+    return MXE_OK;
+}
+
+// The division for launch L from per-tube step estimates (indexed by tube);
+// sets L->nA and trims L->fill.  Without estimates (est == NULL) there is no
+// fill launch.
 static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L, const std::vector<double>* est) {
     const int n = c->ntubes;
     L->nA = n;
@@ -938,27 +978,14 @@ static void tube_fill_split(const mxe_ctx* c, TubeLaunch* L, const std::vector<d
         L->fill = 0;
         return;
     }
-    const int C = L->nt - 2;
-    std::vector<double> team(n), solo(n);
-    double TA = 0.0;
+    std::vector<int> cells(n);
+    std::vector<double> steps(n);
     for (int q = 0; q < n; ++q) {
-        const TubeDesc& d = c->tdesc[c->order_h[q]];
-        const double steps = (*est)[c->order_h[q]];
-        const int ch = (d.n + C - 1) / C;
-        team[q] = (double)((ch + L->cl - 1) / L->cl) * steps / L->teams;
-        solo[q] = (double)ch * steps;
-        TA += team[q];
+        cells[q] = c->tdesc[c->order_h[q]].n;
+        steps[q] = (*est)[c->order_h[q]];
     }
-    double TB = 0.0;
-    int nA = n;
-    while (nA > 1) {
-        const int q = nA - 1;
-        const double ta = TA - team[q], tb = TB + solo[q] / L->fill;
-        if (tb > ta || solo[q] > ta) break;
-        TA = ta;
-        TB = tb;
-        nA = q;
-    }
+    const int nA = plan_fill(n, cells.data(), steps.data(), L->nt - 2, L->cl, L->teams, L->fill,
+                             nullptr);
     L->nA = nA;
     L->fill = nA < n ? std::min(L->fill, n - nA) : 0;
 }
